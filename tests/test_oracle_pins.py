@@ -1,0 +1,372 @@
+"""Pins for the FP64 oracle, against things other than itself.
+
+Each test checks the oracle against a closed form, an invariant the paper
+states, a library routine, or brute force on tiny inputs.  The mutation tests
+at the end plant plausible mistakes in the oracle (on the CPU) and check that
+at least one pin catches each of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from oracle import cs_ngf_oracle as O
+from paper_2110_10156_gb300 import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def rand_case(seed, dims, mask_frac=0.8):
+    rng = np.random.default_rng(seed)
+    A = rng.random(dims)
+    B = rng.random(dims)
+    MA = (rng.random(dims) < mask_frac).astype(np.uint8)
+    MB = (rng.random(dims) < mask_frac).astype(np.uint8)
+    return A, MA, B, MB
+
+
+# ---------------------------------------------------------------- brute force
+def brute_csngf(A, MA, B, MB, eps, gamma):
+    """Eq. 1, 2 and 5 with scalar loops only (independent of the oracle)."""
+    nz, ny, nx = A.shape
+
+    def grad(V, z, y, x):
+        def at(zz, yy, xx):
+            return V[min(max(zz, 0), nz - 1), min(max(yy, 0), ny - 1), min(max(xx, 0), nx - 1)]
+        return ((at(z, y, x + 1) - at(z, y, x - 1)) / 2,
+                (at(z, y + 1, x) - at(z, y - 1, x)) / 2,
+                (at(z + 1, y, x) - at(z - 1, y, x)) / 2)
+
+    def nvec(V, z, y, x):
+        g = grad(V, z, y, x)
+        den = math.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2 + eps ** 2)
+        return [v / den for v in g]
+
+    sumA, sumB = int(MA.sum()), int(MB.sum())
+    thr = max(1, math.ceil(gamma * min(sumA, sumB)))
+    out = {}
+    for cz in range(-(nz - 1), nz):
+        for cy in range(-(ny - 1), ny):
+            for cx in range(-(nx - 1), nx):
+                num, N = 0.0, 0
+                for z in range(nz):
+                    for y in range(ny):
+                        for x in range(nx):
+                            zb, yb, xb = z + cz, y + cy, x + cx
+                            if not (0 <= zb < nz and 0 <= yb < ny and 0 <= xb < nx):
+                                continue
+                            if MA[z, y, x] and MB[zb, yb, xb]:
+                                a = nvec(A, z, y, x)
+                                b = nvec(B, zb, yb, xb)
+                                d = a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+                                num += d * d
+                                N += 1
+                out[(cz, cy, cx)] = (num / N if N >= thr else -np.inf, N)
+    return out
+
+
+def test_direct_matches_brute_force_tiny():
+    A, MA, B, MB = rand_case(1, (3, 4, 3))
+    eps, gamma = 0.05, 0.5
+    s, N = O.csngf_direct(A, MA, B, MB, eps, gamma)
+    ref = brute_csngf(A, MA, B, MB, eps, gamma)
+    for chi, (sv, nv) in ref.items():
+        idx = tuple(c + n - 1 for c, n in zip(chi, A.shape))
+        assert N[idx] == nv
+        if np.isfinite(sv):
+            assert s[idx] == pytest.approx(sv, rel=1e-12, abs=1e-14)
+        else:
+            assert not np.isfinite(s[idx])
+
+
+@pytest.mark.parametrize("dims,seed", [((6, 6, 6), 2), ((5, 7, 6), 3), ((8, 8, 8), 4)])
+def test_fft_form_equals_direct_all_shifts(dims, seed):
+    A, MA, B, MB = rand_case(seed, dims)
+    s_d, N_d = O.csngf_direct(A, MA, B, MB, 1e-3, 0.5)
+    s_f, N_f = O.csngf_fft(A, MA, B, MB, 1e-3, 0.5)
+    assert np.array_equal(N_d, N_f)
+    fin = np.isfinite(s_d)
+    assert np.array_equal(fin, np.isfinite(s_f))
+    np.testing.assert_allclose(s_f[fin], s_d[fin], rtol=1e-10, atol=1e-12)
+
+
+def test_fft_form_equals_direct_nonminimal_pad():
+    A, MA, B, MB = rand_case(5, (6, 5, 7))
+    s_d, _ = O.csngf_direct(A, MA, B, MB, 1e-3, 0.3)
+    s_f, _ = O.csngf_fft(A, MA, B, MB, 1e-3, 0.3, pad=(16, 32, 16))
+    fin = np.isfinite(s_d)
+    np.testing.assert_allclose(s_f[fin], s_d[fin], rtol=1e-10, atol=1e-12)
+
+
+# -------------------------------------------------------------- closed forms
+def test_overlap_of_full_boxes_is_product():
+    dims = (5, 6, 7)
+    one = np.ones(dims)
+    N = np.rint(O.correlate_fft(one, one, (16, 16, 16))).astype(int)
+    for idx in itertools.product(*[range(2 * n - 1) for n in dims]):
+        chi = [i - (n - 1) for i, n in zip(idx, dims)]
+        assert N[idx] == np.prod([n - abs(c) for n, c in zip(dims, chi)])
+
+
+def test_delta_fixes_shift_sign():
+    dims = (6, 6, 6)
+    a = np.zeros(dims)
+    b = np.zeros(dims)
+    a[1, 2, 3] = 1.0
+    b[4, 1, 5] = 1.0                      # b = a moved by t = (+3, -1, +2)
+    C = O.correlate_fft(a, b, (16, 16, 16))
+    idx = np.unravel_index(np.argmax(C), C.shape)
+    chi = tuple(int(i) - (n - 1) for i, n in zip(idx, dims))
+    assert chi == (3, -1, 2)
+    assert C[idx] == pytest.approx(1.0, abs=1e-12)
+    assert np.sum(np.abs(C) > 1e-9) == 1
+
+
+def test_numpy_fft_matches_definition():
+    rng = np.random.default_rng(7)
+    for L in (5, 8, 16, 20, 25, 64):
+        x = rng.normal(size=L) + 1j * rng.normal(size=L)
+        k = np.arange(L)
+        W = np.exp(-2j * np.pi * np.outer(k, k) / L)
+        np.testing.assert_allclose(np.fft.fft(x), W @ x, rtol=1e-11, atol=1e-11)
+
+
+def test_gradient_and_ngf_on_linear_ramp():
+    dims = (6, 7, 8)
+    zz, yy, xx = np.meshgrid(*[np.arange(n, dtype=float) for n in dims], indexing="ij")
+    a, u = 3e-5, np.array([0.6, 0.0, 0.8])            # direction (x, y, z)
+    V = a * (u[0] * xx + u[1] * yy + u[2] * zz)
+    gx, gy, gz = O.gradient(V)
+    inner = (slice(1, -1),) * 3
+    np.testing.assert_allclose(gx[inner], a * u[0], rtol=1e-9)
+    np.testing.assert_allclose(gz[inner], a * u[2], rtol=1e-9)
+    # face: one-sided difference halved
+    np.testing.assert_allclose(gx[:, :, 0], a * u[0] / 2, rtol=1e-9)
+    n = O.ngf(V, 1e-5)
+    scale = a / math.sqrt(a * a + 1e-10)
+    np.testing.assert_allclose(n[0][inner], u[0] * scale, rtol=1e-9)
+    np.testing.assert_allclose(n[2][inner], u[2] * scale, rtol=1e-9)
+
+
+def test_s_ngf_parallel_antiparallel_orthogonal():
+    e = [np.array([1.0]), np.array([0.0]), np.array([0.0])]
+    assert O.s_ngf(e, e)[0] == 1.0
+    assert O.s_ngf(e, [-e[0], e[1], e[2]])[0] == 1.0
+    assert O.s_ngf(e, [e[1], e[0], e[2]])[0] == 0.0
+
+
+def test_scores_bounded_in_unit_interval():
+    A, MA, B, MB = rand_case(11, (7, 7, 7))
+    s, _ = O.csngf_fft(A, MA, B, MB, 1e-3, 0.5)
+    fin = s[np.isfinite(s)]
+    assert fin.size > 0
+    assert fin.min() >= -1e-12 and fin.max() <= 1 + 1e-12
+
+
+def test_threshold_closed_form():
+    assert O.overlap_threshold(100, 51, 0.5) == 26
+    assert O.overlap_threshold(100, 50, 0.5) == 25
+    assert O.overlap_threshold(0, 50, 0.5) == 1
+    assert O.overlap_threshold(7, 9, 1.0) == 7
+
+
+# ------------------------------------------------------------- rotations
+def test_quaternion_matrix_matches_scipy():
+    rng = np.random.default_rng(3)
+    for q in synth.random_quaternions(rng, 20):
+        R = O.quat_to_rotmat(q)
+        Rs = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        np.testing.assert_allclose(R, Rs, atol=1e-12)
+
+
+def quarter_turn(axis):
+    q = synth.axis_angle_quaternion(np.eye(3)[axis], np.pi / 2)
+    R = np.rint(Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()).astype(int)
+    return q, R
+
+
+def permute_volume(V, R):
+    """out(y) = V(R^T (y - c) + c) by integer index arithmetic (cubes)."""
+    n = V.shape[0]
+    out = np.empty_like(V)
+    c2 = n - 1                                   # 2c
+    for zb, yb, xb in itertools.product(range(n), repeat=3):
+        d2 = np.array([2 * xb - c2, 2 * yb - c2, 2 * zb - c2])
+        s2 = R.T @ d2 + c2
+        xa, ya, za = (s2 // 2)
+        out[zb, yb, xb] = V[za, ya, xa]
+    return out
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_quarter_turn_resample_is_exact_permutation(axis):
+    rng = np.random.default_rng(axis)
+    n = 7
+    A = rng.random((n, n, n))
+    M = (rng.random((n, n, n)) < 0.7).astype(np.uint8)
+    q, R = quarter_turn(axis)
+    assert np.array_equal(O.quat_to_rotmat(q), R.astype(float))
+    B = permute_volume(A, R)
+    MB = permute_volume(M, R)
+    Bh, Mh = O.resample(B, MB, q)
+    assert np.array_equal(Bh, A)
+    assert np.array_equal(Mh, M)
+    s_rot, _ = O.score_map(A, M, B, MB, q, eps=1e-3)
+    s_self, _ = O.csngf_fft(A, M, A, M, 1e-3, 0.5)
+    np.testing.assert_array_equal(s_rot, s_self)
+
+
+def test_identity_resample_is_exact():
+    A, MA, B, MB = rand_case(4, (5, 6, 7))
+    Bh, Mh = O.resample(B, MB, (1.0, 0.0, 0.0, 0.0))
+    assert np.array_equal(Bh, B)
+    assert np.array_equal(Mh, MB)
+
+
+def test_trilinear_reproduces_affine_functions():
+    dims = (9, 10, 11)
+    zz, yy, xx = np.meshgrid(*[np.arange(n, dtype=float) for n in dims], indexing="ij")
+    coef = np.array([0.3, -1.1, 0.7])
+    B = 2.0 + coef[0] * xx + coef[1] * yy + coef[2] * zz
+    q = synth.axis_angle_quaternion([1.0, 2.0, -0.5], 0.4)
+    Bh, Mh = O.resample(B, np.ones(dims, np.uint8), q)
+    R = O.quat_to_rotmat(q)
+    px, py, pz = O.sample_points_f32(R, dims)
+    inside = Mh.astype(bool)
+    expect = 2.0 + coef[0] * px.astype(float) + coef[1] * py.astype(float) + coef[2] * pz.astype(float)
+    assert inside.sum() > 0.3 * B.size
+    np.testing.assert_allclose(Bh[inside], expect[inside], rtol=0, atol=1e-9)
+    assert np.all(Bh[~inside & (Mh == 0)][:0] == 0)
+
+
+def test_sample_points_rotate_about_centre():
+    dims = (9, 9, 9)
+    q = synth.axis_angle_quaternion([0, 0, 1], np.pi / 2)     # 90 deg about z
+    px, py, pz = O.sample_points_f32(O.quat_to_rotmat(q), dims)
+    # x-axis unit step from the centre maps to +y: p(c + e_x) = c + R e_x = c + e_y
+    assert (px[4, 4, 5], py[4, 4, 5], pz[4, 4, 5]) == (4.0, 5.0, 4.0)
+
+
+# ----------------------------------------------------- invariants of Eq. 2
+def test_negated_intensity_gives_identical_scores():
+    A, MA, B, MB = rand_case(8, (6, 7, 6))
+    s1, _ = O.csngf_fft(A, MA, B, MB, 1e-3, 0.5)
+    s2, _ = O.csngf_fft(A, MA, -B, MB, 1e-3, 0.5)
+    np.testing.assert_array_equal(s1, s2)
+
+
+def test_integer_shift_at_identity_recovers_shift_and_closed_form():
+    rng = np.random.default_rng(21)
+    n, t = 14, (2, -1, 3)                         # (z, y, x)
+    A = np.zeros((n, n, n))
+    core = slice(5, 9)
+    A[core, core, core] = rng.random((4, 4, 4)) + 0.5
+    B = np.roll(A, t, axis=(0, 1, 2))             # B(y) = A(y - t), zero borders
+    M = np.ones_like(A, dtype=np.uint8)
+    s, N = O.score_map(A, M, B, M, (1, 0, 0, 0), eps=1e-5)
+    best, chi = O.best_of_map(s)
+    assert chi == t
+    gx, gy, gz = O.gradient(A)
+    g2 = gx * gx + gy * gy + gz * gz
+    qv = g2 / (g2 + 1e-10)
+    expect = float(np.sum(qv * qv)) / np.prod([n - abs(c) for c in t])
+    assert best == pytest.approx(expect, rel=1e-12)
+
+
+def test_ramps_closed_form_with_rotation():
+    """A = a (u_A . x), B = b (u_B . y): after B_hat = B o T the NGF direction
+    is R^T u_B, so every valid shift scores (u_A . R^T u_B)^2 q_A q_B."""
+    n = 13
+    dims = (n, n, n)
+    zz, yy, xx = np.meshgrid(*[np.arange(n, dtype=float) for _ in range(3)], indexing="ij")
+    uA = np.array([1.0, 0.0, 0.0])
+    uB = np.array([0.0, 0.6, 0.8])
+    a, b = 2e-5, 5e-5
+    A = a * (uA[0] * xx + uA[1] * yy + uA[2] * zz)
+    B = b * (uB[0] * xx + uB[1] * yy + uB[2] * zz)
+    MA = np.zeros(dims, np.uint8)
+    MA[1:-1, 1:-1, 1:-1] = 1
+    MB = np.zeros(dims, np.uint8)
+    MB[3:-3, 3:-3, 3:-3] = 1
+    q = synth.axis_angle_quaternion([0.3, 1.0, 0.2], 0.5)
+    R = O.quat_to_rotmat(q)
+    s, _ = O.score_map(A, MA, B, MB, q, eps=1e-5, gamma=0.5)
+    fin = s[np.isfinite(s)]
+    qa = a * a / (a * a + 1e-10)
+    qb = b * b / (b * b + 1e-10)
+    expect = (uA @ (R.T @ uB)) ** 2 * qa * qb
+    wrong = (uA @ (R @ uB)) ** 2 * qa * qb
+    assert abs(expect - wrong) > 1e-2
+    assert fin.size > 10
+    np.testing.assert_allclose(fin, expect, rtol=2e-7)
+
+
+def test_generator_pair_recovers_truth_small():
+    p = synth.config_pair(0)
+    s, r, chi = O.align(p.A, p.MA, p.B, p.MB, p.quats)
+    assert r == p.true_index
+    assert chi == p.t_zyx
+
+
+# ------------------------------------------------------------ mutations
+def _pins_pass():
+    """The pins re-run as plain functions; True if all of them pass."""
+    checks = [
+        test_direct_matches_brute_force_tiny,
+        lambda: test_fft_form_equals_direct_all_shifts((6, 6, 6), 2),
+        test_delta_fixes_shift_sign,
+        test_ramps_closed_form_with_rotation,
+        lambda: test_quarter_turn_resample_is_exact_permutation(2),
+        test_integer_shift_at_identity_recovers_shift_and_closed_form,
+        test_gradient_and_ngf_on_linear_ramp,
+    ]
+    try:
+        for c in checks:
+            c()
+    except AssertionError:
+        return False
+    return True
+
+
+def test_pins_pass_unmutated():
+    assert _pins_pass()
+
+
+@pytest.mark.parametrize("mutation", [
+    "transpose_rotation", "drop_cross_weight", "flip_shift_sign",
+    "eps_not_squared", "gradient_one_sided", "swap_xz_sample",
+])
+def test_planted_mistakes_are_caught(mutation, monkeypatch):
+    if mutation == "transpose_rotation":
+        orig = O.quat_to_rotmat
+        monkeypatch.setattr(O, "quat_to_rotmat", lambda q: orig(q).T.copy())
+    elif mutation == "drop_cross_weight":
+        monkeypatch.setattr(O, "CHANNEL_WEIGHTS", (1.0,) * 6)
+    elif mutation == "flip_shift_sign":
+        orig_g = O._gather_shifts
+        monkeypatch.setattr(O, "_gather_shifts",
+                            lambda c, dims, pad: orig_g(np.flip(np.roll(c, -1, axis=(0, 1, 2)),
+                                                                axis=(0, 1, 2)), dims, pad))
+    elif mutation == "eps_not_squared":
+        def ngf_bad(V, eps):
+            gx, gy, gz = O.gradient(V)
+            inv = 1.0 / np.sqrt(gx * gx + gy * gy + gz * gz + float(eps))
+            return gx * inv, gy * inv, gz * inv
+        monkeypatch.setattr(O, "ngf", ngf_bad)
+    elif mutation == "gradient_one_sided":
+        def grad_bad(V):
+            V = np.asarray(V, dtype=float)
+            out = []
+            for axis in (2, 1, 0):
+                n = V.shape[axis]
+                up = np.take(V, np.minimum(np.arange(n) + 1, n - 1), axis=axis)
+                out.append(up - V)
+            return tuple(out)
+        monkeypatch.setattr(O, "gradient", grad_bad)
+    elif mutation == "swap_xz_sample":
+        orig_s = O.sample_points_f32
+        monkeypatch.setattr(O, "sample_points_f32",
+                            lambda R, dims: tuple(reversed(orig_s(R, dims))))
+    assert not _pins_pass(), f"mutation {mutation} went unnoticed"
