@@ -1,0 +1,185 @@
+/*
+ * cs_ngf.h -- C ABI of the GB300 all-shift NGF similarity library
+ *             (hot path of Cross-Sim-NGF global rigid alignment).
+ *
+ * What it computes (Cross-Sim-NGF, Ofverstedt, Lindblad, Sladoje):
+ *   n(x; V)     = grad V / sqrt(|grad V|^2 + eps^2)                  Eq. 1
+ *   s_NGF(x)    = <n(x; A), n(x; B)>^2                               Eq. 2
+ *   CSNGF(chi)  = sum_x M_A(x) M_B(x+chi) s_NGF(x; A(x), B(x+chi)) / N(chi),
+ *   N(chi)      = (M_A star M_B)(chi)                                Eq. 4-5
+ * evaluated for every integer shift chi at once through six weighted channel
+ * correlations and one mask correlation in the frequency domain, summed
+ * before the inverse transform (Eq. 6-8, Section 3.1).  For each candidate
+ * rotation the floating volume is resampled, B_hat = B o T_theta, with
+ * trilinear interpolation, shifts whose overlap is below gamma are excluded,
+ * and the best shift is argmax_chi CSNGF (Section 3.2); the alignment is the
+ * maximum over rotations (Fig. 1).
+ *
+ * Conventions (the paper leaves these open; the library fixes them):
+ *   - Volumes are [z][y][x] with x contiguous; dims[] = {nz, ny, nx}, each in
+ *     [2, 256].  B has the same dims as A.
+ *   - Vectors are (x, y, z).  Rotation centre c = (n - 1) / 2 per axis and
+ *     B_hat(x) = B(R(q)(x - c) + c), R the Hamilton matrix of the unit
+ *     quaternion q = (w, x, y, z), built in FP64 on the host with entries
+ *     within 1e-9 of -1, 0, 1 snapped, then rounded to FP32.
+ *   - The rotated mask is [trilinear M_B >= 0.5] at sample points inside
+ *     [0, n-1]^3 (1e-4 slack); outside, B_hat = 0 and the mask is 0.
+ *   - Gradient: central differences, unit spacing, indices clamped at faces.
+ *   - Shift sign: C(chi) = sum_x a(x) b(x + chi); shifts are reported as
+ *     (chi_z, chi_y, chi_x) in [-(n-1), n-1].
+ *   - A shift is valid iff N(chi) >= max(1, ceil(gamma * min(sum M_A,
+ *     sum M_hat))).  Masks are 0/1 bytes (nonzero counts as 1).
+ *   - Ties: the larger score wins; equal scores go to the smallest
+ *     (chi_z, chi_y, chi_x), then to the smallest rotation index.
+ *   - FFT lengths: per axis the smallest of {16, 32, 64, 128, 160, 200, 256,
+ *     320, 400, 512} that is >= 2n - 1 (full linear correlation), unless set.
+ *
+ * Memory and streams: array arguments are DEVICE pointers owned by the
+ * caller unless a function says "host".  Work is enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream); the caller keeps the inputs
+ * alive until that work completes.  A handle owns all of its device memory
+ * (fixed spectra and per-batch workspace) and is used by one host thread at
+ * a time.  No function aborts the process: each returns a status.
+ */
+#ifndef CS_NGF_H
+#define CS_NGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_ngf_fixed cs_ngf_fixed; /* opaque handle */
+
+typedef enum {
+  CS_NGF_OK = 0,
+  CS_NGF_EINVAL = 1,      /* bad argument (null pointer, size, eps, gamma, quaternion) */
+  CS_NGF_ENOMEM = 2,      /* device or host allocation failed */
+  CS_NGF_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  CS_NGF_ENOVALID = 4,    /* no rotation had any valid shift */
+  CS_NGF_EUNSUPPORTED = 5 /* FFT length or size not supported */
+} cs_ngf_status;
+
+typedef struct {
+  float eps;        /* Eq. 1 regulariser; the paper uses 1e-5 */
+  float gamma;      /* minimum overlap fraction in (0, 1]; the paper uses 0.5 */
+  int32_t pad[3];   /* FFT lengths (z, y, x); 0 = automatic */
+  int32_t batch;    /* rotations per launch group; 0 = automatic (memory-sized) */
+} cs_ngf_config;
+
+typedef struct {
+  int32_t dims[3];              /* nz, ny, nx */
+  int32_t pad[3];               /* FFT lengths in use */
+  int32_t batch;                /* rotations per launch group */
+  int64_t sum_mask_a;           /* sum of M_A */
+  int64_t fixed_bytes;          /* device bytes of the fixed spectra */
+  int64_t workspace_bytes;      /* device bytes of the per-batch workspace */
+} cs_ngf_info;
+
+/* Fill *cfg with the paper's settings (eps 1e-5, gamma 0.5, automatic pad and
+ * batch). */
+void cs_ngf_default_config(cs_ngf_config* cfg);
+
+/* Section 3.1, Eq. 1, 6-8, A side: the NGF of the fixed volume A, its six
+ * channels times M_A and M_A itself, their forward 3D FFTs, conjugated and
+ * weighted (1,1,1,2,2,2), stored on the device in the new handle.
+ *   A      device float32 [nz][ny][nx]
+ *   maskA  device uint8   [nz][ny][nx]
+ *   dims   host {nz, ny, nx}
+ *   cfg    host, NULL = defaults
+ *   out    host; receives the handle (NULL on failure)
+ * Synchronises `stream` before returning (the handle's sum of M_A is read
+ * back).  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const int32_t dims[3],
+                                   const cs_ngf_config* cfg, void* stream, cs_ngf_fixed** out);
+
+/* Section 3.2 + Eq. 5: for each of R rotations, resample B, compute CSNGF for
+ * every valid shift and return its maximum and location.
+ *   B, maskB    device, dims of the handle
+ *   quats       host float64 [R][4] (w, x, y, z); normalised here; a
+ *               quaternion whose norm differs from 1 by more than 1e-3 is EINVAL
+ *   best_score  device float32 [R]; -inf where a rotation has no valid shift
+ *   best_shift  device int32 [R][3] (chi_z, chi_y, chi_x); 0 where no valid shift
+ * Asynchronous on `stream` except for the small host-to-device upload of the
+ * rotation matrices, which is staged through the handle (the call returns
+ * once its work is enqueued).  Errors: EINVAL, ECUDA. */
+cs_ngf_status cs_ngf_score_rotations(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                                     const double* quats, int32_t R, float* best_score,
+                                     int32_t* best_shift, void* stream);
+
+/* cs_ngf_score_rotations with HOST buffers: copies B and maskB (host,
+ * [nz][ny][nx]) to the handle's device staging area, scores, and copies the
+ * results back to host best_score [R] / best_shift [R][3].  Synchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+cs_ngf_status cs_ngf_score_rotations_host(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                                          const double* quats, int32_t R, float* best_score,
+                                          int32_t* best_shift, void* stream);
+
+/* Fig. 1: the maximum of s_ANGF over all rotations and shifts.
+ *   score, rot_index, shift: HOST outputs (score -inf, index -1 if nothing
+ *   is valid, with status ENOVALID).  Synchronous.  B, maskB device. */
+cs_ngf_status cs_ngf_align(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                           const double* quats, int32_t R, float* score, int32_t* rot_index,
+                           int32_t shift[3], void* stream);
+
+/* Eq. 5 for one rotation, the full map: map is device float32
+ * [2nz-1][2ny-1][2nx-1] indexed by chi + n - 1, holding CSNGF(chi) or -inf
+ * where chi is not valid.  quat: host float64 [4].  Errors: EINVAL, ECUDA. */
+cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                               const double* quat, float* map, void* stream);
+
+/* Section 3.2 resample alone (one rotation): B_hat device float32 and M_hat
+ * device uint8, [nz][ny][nx].  quat: host float64 [4]. */
+cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                              const double* quat, float* Bhat, uint8_t* Mhat, void* stream);
+
+/* Recompute the fixed-volume spectra of an existing handle from a new A and
+ * maskA of the same dims (no reallocation).  Synchronises `stream`.
+ * Errors: EINVAL, ECUDA. */
+cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* maskA,
+                                  void* stream);
+
+/* Per-stage timing.  While profiling is on, every kernel launch of the handle
+ * is bracketed by CUDA events recorded on its stream.  cs_ngf_stage_times
+ * waits for them and returns, per stage, the summed milliseconds and the
+ * number of launches since the previous call (host arrays of
+ * CS_NGF_NSTAGES), then forgets them.  Stages: */
+#define CS_NGF_NSTAGES 8
+enum {
+  CS_NGF_STAGE_RESAMPLE = 0, /* Section 3.2 trilinear resample + rotated mask */
+  CS_NGF_STAGE_FWD_X = 1,    /* Eq. 1, 6: NGF channels + x-axis FFT */
+  CS_NGF_STAGE_FWD_Y = 2,    /* y-axis FFT */
+  CS_NGF_STAGE_ZMAC = 3,     /* z-axis FFT, Eq. 7-8 spectral sum, z-axis inverse */
+  CS_NGF_STAGE_INV_Y = 4,    /* y-axis inverse FFT */
+  CS_NGF_STAGE_INV_X = 5,    /* x-axis inverse FFT, Eq. 5 normalisation, argmax */
+  CS_NGF_STAGE_FIXED = 6,    /* fixed-volume spectra (prepare / update) */
+  CS_NGF_STAGE_OTHER = 7     /* thresholds, result decoding */
+};
+cs_ngf_status cs_ngf_set_profiling(cs_ngf_fixed* f, int32_t on);
+cs_ngf_status cs_ngf_stage_times(cs_ngf_fixed* f, double* ms, int64_t* launches);
+
+/* Number of kernel launches this library has made in the process. */
+int64_t cs_ngf_launch_count(void);
+
+/* Sizes and FFT lengths of a handle.  info: host. */
+cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info);
+
+/* Free every device allocation of the handle (NULL is a no-op).  The caller
+ * makes sure no work that uses the handle is still in flight. */
+void cs_ngf_release(cs_ngf_fixed* f);
+
+/* Static description of a status code. */
+const char* cs_ngf_status_string(int32_t status);
+
+/* Detail of the last failure on the calling host thread ("" if none). */
+const char* cs_ngf_last_error(void);
+
+/* Automatic FFT length for a volume side n (0 if n is unsupported). */
+int32_t cs_ngf_auto_pad(int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CS_NGF_H */

@@ -1,0 +1,280 @@
+"""Thin Python binding of ``libcs_ngf.so`` (C ABI in ``include/cs_ngf.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device arrays are passed as torch CUDA tensors (their data pointers
+and the current torch stream); quaternions are host float64.  If the library
+has not been built the import fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcs_ngf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_2110_10156_gb300.build` (needs nvcc)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ENOVALID, EUNSUPPORTED = range(6)
+
+EXPORTED = (
+    "cs_ngf_default_config", "cs_ngf_prepare_fixed", "cs_ngf_score_rotations",
+    "cs_ngf_score_rotations_host", "cs_ngf_align", "cs_ngf_score_map", "cs_ngf_resample",
+    "cs_ngf_get_info", "cs_ngf_release", "cs_ngf_status_string", "cs_ngf_last_error",
+    "cs_ngf_auto_pad", "cs_ngf_update_fixed", "cs_ngf_set_profiling", "cs_ngf_stage_times",
+    "cs_ngf_launch_count",
+)
+
+STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "other")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("pad", ctypes.c_int32 * 3),
+                ("batch", ctypes.c_int32), ("sum_mask_a", ctypes.c_int64),
+                ("fixed_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+_vp, _i32, _p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER
+_lib.cs_ngf_default_config.argtypes = [_p(Config)]
+_lib.cs_ngf_default_config.restype = None
+_lib.cs_ngf_prepare_fixed.argtypes = [_vp, _vp, _p(_i32), _p(Config), _vp, _p(_vp)]
+_lib.cs_ngf_score_rotations.argtypes = [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]
+_lib.cs_ngf_score_rotations_host.argtypes = [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]
+_lib.cs_ngf_align.argtypes = [_vp, _vp, _vp, _vp, _i32, _p(ctypes.c_float), _p(_i32), _p(_i32), _vp]
+_lib.cs_ngf_score_map.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.cs_ngf_resample.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.cs_ngf_get_info.argtypes = [_vp, _p(Info)]
+_lib.cs_ngf_release.argtypes = [_vp]
+_lib.cs_ngf_release.restype = None
+_lib.cs_ngf_status_string.argtypes = [_i32]
+_lib.cs_ngf_status_string.restype = ctypes.c_char_p
+_lib.cs_ngf_last_error.argtypes = []
+_lib.cs_ngf_last_error.restype = ctypes.c_char_p
+_lib.cs_ngf_auto_pad.argtypes = [_i32]
+_lib.cs_ngf_auto_pad.restype = _i32
+_lib.cs_ngf_update_fixed.argtypes = [_vp, _vp, _vp, _vp]
+_lib.cs_ngf_set_profiling.argtypes = [_vp, _i32]
+_lib.cs_ngf_stage_times.argtypes = [_vp, _p(ctypes.c_double), _p(ctypes.c_int64)]
+_lib.cs_ngf_launch_count.argtypes = []
+_lib.cs_ngf_launch_count.restype = ctypes.c_int64
+for _name in ("cs_ngf_update_fixed", "cs_ngf_set_profiling", "cs_ngf_stage_times",
+              "cs_ngf_prepare_fixed", "cs_ngf_score_rotations", "cs_ngf_score_rotations_host",
+              "cs_ngf_align", "cs_ngf_score_map", "cs_ngf_resample", "cs_ngf_get_info"):
+    getattr(_lib, _name).restype = _i32
+
+
+class CsNgfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.cs_ngf_status_string(status).decode()
+        detail = _lib.cs_ngf_last_error().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({detail})" if detail else ""))
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise CsNgfError(status, where)
+
+
+def library():
+    """The loaded ctypes library (for symbol checks)."""
+    return _lib
+
+
+def launch_count() -> int:
+    """Kernel launches made by the library in this process."""
+    return int(_lib.cs_ngf_launch_count())
+
+
+def auto_pad(n: int) -> int:
+    return int(_lib.cs_ngf_auto_pad(int(n)))
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _quats(q) -> np.ndarray:
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1, 4))
+    return q
+
+
+class Fixed:
+    """Handle on the device-resident fixed-volume spectra (cs_ngf_prepare_fixed)."""
+
+    def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None):
+        import torch
+        if A.dim() != 3:
+            raise ValueError("A must be [nz][ny][nx]")
+        self.dims = tuple(int(d) for d in A.shape)
+        if tuple(MA.shape) != self.dims:
+            raise ValueError("maskA must have A's shape")
+        cfg = Config()
+        _lib.cs_ngf_default_config(ctypes.byref(cfg))
+        cfg.eps = float(eps)
+        cfg.gamma = float(gamma)
+        if pad is not None:
+            for i, p in enumerate(pad):
+                cfg.pad[i] = int(p)
+        cfg.batch = int(batch)
+        dims = (ctypes.c_int32 * 3)(*self.dims)
+        h = ctypes.c_void_p()
+        st = _check(_lib.cs_ngf_prepare_fixed(_dev_ptr(A, torch.float32, "A"),
+                                              _dev_ptr(MA, torch.uint8, "maskA"), dims,
+                                              ctypes.byref(cfg), _stream_ptr(stream),
+                                              ctypes.byref(h)), "cs_ngf_prepare_fixed")
+        self._h = h
+        self._keep = (A, MA)
+        info = Info()
+        _check(_lib.cs_ngf_get_info(self._h, ctypes.byref(info)), "cs_ngf_get_info")
+        self.pad = tuple(info.pad)
+        self.batch = int(info.batch)
+        self.sum_mask_a = int(info.sum_mask_a)
+        self.fixed_bytes = int(info.fixed_bytes)
+        self.workspace_bytes = int(info.workspace_bytes)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check_vol(self, B, MB):
+        import torch
+        if tuple(B.shape) != self.dims or tuple(MB.shape) != self.dims:
+            raise ValueError("B and maskB must have the fixed volume's shape")
+        return _dev_ptr(B, torch.float32, "B"), _dev_ptr(MB, torch.uint8, "maskB")
+
+    def score_rotations(self, B, MB, quats, out_score=None, out_shift=None, stream=None):
+        """Per-rotation best score [R] (float32) and shift [R, 3] (int32, z y x)."""
+        import torch
+        q = _quats(quats)
+        R = q.shape[0]
+        pb, pm = self._check_vol(B, MB)
+        if out_score is None:
+            out_score = torch.empty(R, dtype=torch.float32, device=B.device)
+        if out_shift is None:
+            out_shift = torch.empty((R, 3), dtype=torch.int32, device=B.device)
+        _check(_lib.cs_ngf_score_rotations(self._h, pb, pm, q.ctypes.data_as(ctypes.c_void_p), R,
+                                           _dev_ptr(out_score, torch.float32, "best_score"),
+                                           _dev_ptr(out_shift, torch.int32, "best_shift"),
+                                           _stream_ptr(stream)), "cs_ngf_score_rotations")
+        self._last_q = q          # keep the host array alive until the call returned
+        return out_score, out_shift
+
+    def score_rotations_host(self, B_host: np.ndarray, MB_host: np.ndarray, quats,
+                             out_score: np.ndarray | None = None,
+                             out_shift: np.ndarray | None = None, stream=None):
+        """Same, from HOST arrays (copies inside the call); returns numpy arrays."""
+        q = _quats(quats)
+        R = q.shape[0]
+        for name, arr, dt in (("B", B_host, np.float32), ("maskB", MB_host, np.uint8)):
+            if arr.dtype != dt or not arr.flags.c_contiguous or tuple(arr.shape) != self.dims:
+                raise ValueError(f"{name} must be a C-contiguous {dt.__name__} array of the fixed shape")
+        if out_score is None:
+            out_score = np.empty(R, np.float32)
+        if out_shift is None:
+            out_shift = np.empty((R, 3), np.int32)
+        _check(_lib.cs_ngf_score_rotations_host(
+            self._h, ctypes.c_void_p(B_host.ctypes.data), ctypes.c_void_p(MB_host.ctypes.data),
+            q.ctypes.data_as(ctypes.c_void_p), R, ctypes.c_void_p(out_score.ctypes.data),
+            ctypes.c_void_p(out_shift.ctypes.data), _stream_ptr(stream)),
+            "cs_ngf_score_rotations_host")
+        return out_score, out_shift
+
+    def align(self, B, MB, quats, stream=None):
+        """(score, rotation index, (cz, cy, cx)); index -1 if nothing is valid."""
+        q = _quats(quats)
+        pb, pm = self._check_vol(B, MB)
+        sc = ctypes.c_float()
+        ri = ctypes.c_int32()
+        sh = (ctypes.c_int32 * 3)()
+        st = _lib.cs_ngf_align(self._h, pb, pm, q.ctypes.data_as(ctypes.c_void_p), q.shape[0],
+                               ctypes.byref(sc), ctypes.byref(ri), sh, _stream_ptr(stream))
+        if st not in (OK, ENOVALID):
+            _check(st, "cs_ngf_align")
+        return float(sc.value), int(ri.value), tuple(int(v) for v in sh)
+
+    def score_map(self, B, MB, quat, stream=None):
+        """Full CSNGF map over shifts for one rotation (-inf where invalid)."""
+        import torch
+        q = _quats(quat)
+        pb, pm = self._check_vol(B, MB)
+        shape = tuple(2 * n - 1 for n in self.dims)
+        out = torch.empty(shape, dtype=torch.float32, device=B.device)
+        _check(_lib.cs_ngf_score_map(self._h, pb, pm, q.ctypes.data_as(ctypes.c_void_p),
+                                     _dev_ptr(out, torch.float32, "map"), _stream_ptr(stream)),
+               "cs_ngf_score_map")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return out
+
+    def resample(self, B, MB, quat, stream=None):
+        """B_hat (float32) and M_hat (uint8) for one rotation."""
+        import torch
+        q = _quats(quat)
+        pb, pm = self._check_vol(B, MB)
+        Bh = torch.empty(self.dims, dtype=torch.float32, device=B.device)
+        Mh = torch.empty(self.dims, dtype=torch.uint8, device=B.device)
+        _check(_lib.cs_ngf_resample(self._h, pb, pm, q.ctypes.data_as(ctypes.c_void_p),
+                                    _dev_ptr(Bh, torch.float32, "Bhat"),
+                                    _dev_ptr(Mh, torch.uint8, "Mhat"), _stream_ptr(stream)),
+               "cs_ngf_resample")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return Bh, Mh
+
+    def update_fixed(self, A, MA, stream=None):
+        """Recompute the fixed spectra from a new A / maskA of the same shape."""
+        import torch
+        if tuple(A.shape) != self.dims or tuple(MA.shape) != self.dims:
+            raise ValueError("A and maskA must keep the handle's shape")
+        _check(_lib.cs_ngf_update_fixed(self._h, _dev_ptr(A, torch.float32, "A"),
+                                        _dev_ptr(MA, torch.uint8, "maskA"), _stream_ptr(stream)),
+               "cs_ngf_update_fixed")
+        self._keep = (A, MA)
+
+    def set_profiling(self, on: bool):
+        _check(_lib.cs_ngf_set_profiling(self._h, 1 if on else 0), "cs_ngf_set_profiling")
+
+    def stage_times(self):
+        """{stage: (milliseconds, launches)} since the previous call (synchronises)."""
+        ms = (ctypes.c_double * len(STAGES))()
+        n = (ctypes.c_int64 * len(STAGES))()
+        _check(_lib.cs_ngf_stage_times(self._h, ms, n), "cs_ngf_stage_times")
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(STAGES)}
+
+    def release(self):
+        if getattr(self, "_h", None):
+            _lib.cs_ngf_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def prepare_fixed(A, MA, **kw) -> Fixed:
+    return Fixed(A, MA, **kw)

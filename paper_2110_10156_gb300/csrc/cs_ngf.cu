@@ -1,0 +1,594 @@
+// C ABI of the all-shift NGF similarity library: handle management, host-side
+// rotation matrices, workspace sizing and the per-batch launch sequence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cs_ngf.h"
+#include "kernels.cuh"
+
+using namespace csngf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cs_ngf_status fail(cs_ngf_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CS_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? CS_NGF_ENOMEM : CS_NGF_ECUDA,          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+constexpr int kPads[] = {16, 32, 64, 128, 160, 200, 256, 320, 400, 512};
+
+bool pad_supported(int p) {
+  for (int v : kPads)
+    if (v == p) return true;
+  return false;
+}
+
+int auto_pad(int n) {
+  for (int v : kPads)
+    if (v >= 2 * n - 1) return v;
+  return 0;
+}
+
+// Hamilton unit quaternion (w, x, y, z) -> row-major matrix on (x, y, z), FP64,
+// entries within 1e-9 of -1, 0, 1 snapped (exact identity and quarter turns).
+void quat_to_rotmat(const double* q, double* R) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  const double s = std::sqrt(w * w + x * x + y * y + z * z);
+  w = w / s;
+  x = x / s;
+  y = y / s;
+  z = z / s;
+  R[0] = 1.0 - 2.0 * (y * y + z * z);
+  R[1] = 2.0 * (x * y - w * z);
+  R[2] = 2.0 * (x * z + w * y);
+  R[3] = 2.0 * (x * y + w * z);
+  R[4] = 1.0 - 2.0 * (x * x + z * z);
+  R[5] = 2.0 * (y * z - w * x);
+  R[6] = 2.0 * (x * z - w * y);
+  R[7] = 2.0 * (y * z + w * x);
+  R[8] = 1.0 - 2.0 * (x * x + y * y);
+  const double targets[3] = {-1.0, 0.0, 1.0};
+  for (double tgt : targets)
+    for (int i = 0; i < 9; ++i)
+      if (std::fabs(R[i] - tgt) <= 1e-9) R[i] = tgt;
+}
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+    dev_ = dev;
+  }
+  ~DeviceGuard() {
+    if (prev_ != dev_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = 0, dev_ = 0;
+};
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+}  // namespace
+
+struct cs_ngf_fixed {
+  int device = 0;
+  Geo g{};
+  float eps = 1e-5f, gamma = 0.5f;
+  int batch = 1;
+  int sumA = 0;
+  size_t f02_elems = 0, f13_elems = 0;
+  float2* UV = nullptr;
+  float* Bh = nullptr;
+  uint8_t* Mh = nullptr;
+  float2* F02 = nullptr;
+  float2* F13 = nullptr;
+  int* msum = nullptr;
+  float* thr = nullptr;
+  unsigned long long* keys = nullptr;
+  float2* tw[3] = {nullptr, nullptr, nullptr};   // z, y, x
+  // rotation matrices: pinned host staging + device copy, grown on demand
+  RotMat* rot_h = nullptr;
+  RotMat* rot_d = nullptr;
+  int rot_cap = 0;
+  cudaEvent_t rot_ev = nullptr;
+  // host-buffer entry point staging
+  float* stage_B = nullptr;
+  uint8_t* stage_M = nullptr;
+  float* res_score = nullptr;
+  int32_t* res_shift = nullptr;
+  int res_cap = 0;
+  size_t fixed_bytes = 0, workspace_bytes = 0;
+  // per-stage CUDA-event timing (cs_ngf_set_profiling)
+  bool profiling = false;
+  struct Span { int stage; cudaEvent_t a, b; };
+  std::vector<Span> spans;
+};
+
+namespace {
+
+std::atomic<long long> g_launches{0};
+
+// brackets one kernel launch: counts it and, when profiling, times it with
+// events on the launching stream
+struct Stage {
+  cs_ngf_fixed* f;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  Stage(cs_ngf_fixed* f_, int s_, cudaStream_t st_) : f(f_), stage(s_), st(st_) {
+    if (f->profiling && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+  }
+  ~Stage() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (a) {
+      cudaEvent_t b = nullptr;
+      if (cudaEventCreate(&b) == cudaSuccess) {
+        cudaEventRecord(b, st);
+        f->spans.push_back({stage, a, b});
+      } else {
+        cudaEventDestroy(a);
+      }
+    }
+  }
+};
+
+// -------------------------------------------------------------- dispatch
+#define CS_DISPATCH(P, CALL)                                                           \
+  switch (P) {                                                                          \
+    case 16: { constexpr int PP = 16; CALL; } break;                                    \
+    case 32: { constexpr int PP = 32; CALL; } break;                                    \
+    case 64: { constexpr int PP = 64; CALL; } break;                                    \
+    case 128: { constexpr int PP = 128; CALL; } break;                                  \
+    case 160: { constexpr int PP = 160; CALL; } break;                                  \
+    case 200: { constexpr int PP = 200; CALL; } break;                                  \
+    case 256: { constexpr int PP = 256; CALL; } break;                                  \
+    case 320: { constexpr int PP = 320; CALL; } break;                                  \
+    case 400: { constexpr int PP = 400; CALL; } break;                                  \
+    case 512: { constexpr int PP = 512; CALL; } break;                                  \
+    default: break;                                                                     \
+  }
+
+cs_ngf_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CS_NGF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return CS_NGF_OK;
+}
+
+void free_handle(cs_ngf_fixed* f) {
+  if (!f) return;
+  DeviceGuard guard(f->device);
+  cudaFree(f->UV);
+  cudaFree(f->Bh);
+  cudaFree(f->Mh);
+  cudaFree(f->F02);
+  cudaFree(f->F13);
+  cudaFree(f->msum);
+  cudaFree(f->thr);
+  cudaFree(f->keys);
+  for (int a = 0; a < 3; ++a) {
+    bool dup = false;
+    for (int b = 0; b < a; ++b) dup |= (f->tw[b] == f->tw[a]);
+    if (!dup) cudaFree(f->tw[a]);
+  }
+  if (f->rot_ev) cudaEventSynchronize(f->rot_ev);
+  for (auto& sp : f->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+  cudaFreeHost(f->rot_h);
+  cudaFree(f->rot_d);
+  if (f->rot_ev) cudaEventDestroy(f->rot_ev);
+  cudaFree(f->stage_B);
+  cudaFree(f->stage_M);
+  cudaFree(f->res_score);
+  cudaFree(f->res_shift);
+  delete f;
+}
+
+cs_ngf_status make_twiddles(int P, float2** out) {
+  std::vector<float2> h(P);
+  for (int m = 0; m < P; ++m) {
+    h[m].x = (float)ctw::cos2pi(m, P);
+    h[m].y = (float)(-ctw::sin2pi(m, P));
+  }
+  CS_CUDA(dalloc(out, (size_t)P));
+  CS_CUDA(cudaMemcpy(*out, h.data(), sizeof(float2) * P, cudaMemcpyHostToDevice));
+  return CS_NGF_OK;
+}
+
+// upload R rotation matrices (host FP64 quaternions) to f->rot_d
+cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* quats, int R, cudaStream_t st) {
+  if (!quats) return fail(CS_NGF_EINVAL, "quats is NULL");
+  for (int r = 0; r < R; ++r) {
+    const double* q = quats + 4 * r;
+    const double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(std::fabs(n - 1.0) <= 1e-3))
+      return fail(CS_NGF_EINVAL, "quaternion " + std::to_string(r) + " is not unit (norm " +
+                                     std::to_string(n) + ")");
+  }
+  if (f->rot_ev) CS_CUDA(cudaEventSynchronize(f->rot_ev));   // previous upload has left rot_h
+  if (R > f->rot_cap) {
+    if (f->rot_ev) CS_CUDA(cudaDeviceSynchronize());          // rot_d may still be read
+    cudaFreeHost(f->rot_h);
+    cudaFree(f->rot_d);
+    f->rot_h = nullptr;
+    f->rot_d = nullptr;
+    f->rot_cap = 0;
+    const int cap = std::max(R, 64);
+    CS_CUDA(cudaMallocHost((void**)&f->rot_h, sizeof(RotMat) * cap));
+    CS_CUDA(dalloc(&f->rot_d, (size_t)cap));
+    f->rot_cap = cap;
+  }
+  if (!f->rot_ev) CS_CUDA(cudaEventCreateWithFlags(&f->rot_ev, cudaEventDisableTiming));
+  for (int r = 0; r < R; ++r) {
+    double Rm[9];
+    quat_to_rotmat(quats + 4 * r, Rm);
+    for (int i = 0; i < 9; ++i) f->rot_h[r].m[i] = (float)Rm[i];
+  }
+  CS_CUDA(cudaMemcpyAsync(f->rot_d, f->rot_h, sizeof(RotMat) * R, cudaMemcpyHostToDevice, st));
+  CS_CUDA(cudaEventRecord(f->rot_ev, st));
+  return CS_NGF_OK;
+}
+
+// the FFT passes for nb volumes already resampled into f->Bh / f->Mh
+cs_ngf_status run_transforms(cs_ngf_fixed* f, int nb, float* map, cudaStream_t st) {
+  const Geo& g = f->g;
+  { Stage sp(f, 1, st); CS_DISPATCH(g.Px, launch_fwd_x<PP>(f->Bh, f->Mh, f->F02, f->tw[2], g, nb, st)); }
+  if (cs_ngf_status s = check_launch("fwd_x")) return s;
+  { Stage sp(f, 2, st); CS_DISPATCH(g.Py, launch_fwd_y<PP>(f->F02, f->F13, f->tw[1], g, nb, st)); }
+  if (cs_ngf_status s = check_launch("fwd_y")) return s;
+  { Stage sp(f, 3, st); CS_DISPATCH(g.Pz, launch_zmac<PP>(f->F13, f->UV, f->F02, f->tw[0], g, nb, st)); }
+  if (cs_ngf_status s = check_launch("zmac")) return s;
+  { Stage sp(f, 4, st); CS_DISPATCH(g.Py, launch_inv_y<PP>(f->F02, f->F13, f->tw[1], g, nb, st)); }
+  if (cs_ngf_status s = check_launch("inv_y")) return s;
+  { Stage sp(f, 5, st); CS_DISPATCH(g.Px, launch_inv_x<PP>(f->F13, f->thr, f->keys, map, f->tw[2], g, nb, st)); }
+  if (cs_ngf_status s = check_launch("inv_x")) return s;
+  return CS_NGF_OK;
+}
+
+// score rotations [r0, r0 + nb) whose matrices are at f->rot_d + r0
+cs_ngf_status score_batch(cs_ngf_fixed* f, const float* B, const uint8_t* MB, int r0, int nb,
+                          float* best_score, int32_t* best_shift, float* map, cudaStream_t st) {
+  const Geo& g = f->g;
+  CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int) * nb, st));
+  CS_CUDA(cudaMemsetAsync(f->keys, 0, sizeof(unsigned long long) * nb, st));
+  {
+    Stage sp(f, 0, st);
+    k_resample<<<dim3((unsigned)(g.nz * g.ny), (unsigned)nb), 128, 0, st>>>(
+        B, MB, f->rot_d + r0, g, f->Bh, f->Mh, f->msum);
+  }
+  if (cs_ngf_status s = check_launch("resample")) return s;
+  const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
+  {
+    Stage sp(f, 7, st);
+    k_thresholds<<<(nb + 127) / 128, 128, 0, st>>>(f->msum, f->sumA, f->gamma, pvol, nb, f->thr);
+  }
+  if (cs_ngf_status s = check_launch("thresholds")) return s;
+  if (cs_ngf_status s = run_transforms(f, nb, map, st)) return s;
+  {
+    Stage sp(f, 7, st);
+    k_finalize<<<(nb + 127) / 128, 128, 0, st>>>(f->keys, nb, g, best_score + r0,
+                                                  best_shift + 3 * (size_t)r0);
+  }
+  return check_launch("finalize");
+}
+
+// Section 3.1 A side: NGF channels of A times M_A, forward FFTs, weights -> f->UV
+cs_ngf_status run_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* MA, cudaStream_t st) {
+  const Geo& g = f->g;
+  { Stage sp(f, 6, st); k_copy_in<<<1024, 256, 0, st>>>(A, MA, g.nvox, f->Bh, f->Mh); }
+  if (cs_ngf_status s = check_launch("copy_in")) return s;
+  CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
+  { Stage sp(f, 6, st); k_mask_sum<<<1024, 256, 0, st>>>(f->Mh, g.nvox, f->msum); }
+  if (cs_ngf_status s = check_launch("mask_sum")) return s;
+  { Stage sp(f, 6, st); CS_DISPATCH(g.Px, launch_fwd_x<PP>(f->Bh, f->Mh, f->F02, f->tw[2], g, 1, st)); }
+  if (cs_ngf_status s = check_launch("fwd_x (fixed)")) return s;
+  { Stage sp(f, 6, st); CS_DISPATCH(g.Py, launch_fwd_y<PP>(f->F02, f->F13, f->tw[1], g, 1, st)); }
+  if (cs_ngf_status s = check_launch("fwd_y (fixed)")) return s;
+  { Stage sp(f, 6, st); CS_DISPATCH(g.Pz, launch_prep_z<PP>(f->F13, f->UV, f->tw[0], g, st)); }
+  if (cs_ngf_status s = check_launch("prep_z")) return s;
+  int sumA = 0;
+  CS_CUDA(cudaMemcpyAsync(&sumA, f->msum, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaStreamSynchronize(st));
+  f->sumA = sumA;
+  return CS_NGF_OK;
+}
+
+cs_ngf_status check_volume_args(const cs_ngf_fixed* f, const float* B, const uint8_t* MB) {
+  if (!f) return fail(CS_NGF_EINVAL, "handle is NULL");
+  if (!B || !MB) return fail(CS_NGF_EINVAL, "B or maskB is NULL");
+  return CS_NGF_OK;
+}
+
+cs_ngf_status score_all(cs_ngf_fixed* f, const float* B, const uint8_t* MB, const double* quats,
+                        int R, float* best_score, int32_t* best_shift, cudaStream_t st) {
+  if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
+  if (!best_score || !best_shift) return fail(CS_NGF_EINVAL, "output pointer is NULL");
+  if (cs_ngf_status s = upload_rotations(f, quats, R, st)) return s;
+  for (int r0 = 0; r0 < R; r0 += f->batch) {
+    const int nb = std::min(f->batch, R - r0);
+    if (cs_ngf_status s = score_batch(f, B, MB, r0, nb, best_score, best_shift, nullptr, st)) return s;
+  }
+  return CS_NGF_OK;
+}
+
+cs_ngf_status ensure_results(cs_ngf_fixed* f, int R) {
+  if (R <= f->res_cap) return CS_NGF_OK;
+  CS_CUDA(cudaDeviceSynchronize());
+  cudaFree(f->res_score);
+  cudaFree(f->res_shift);
+  f->res_score = nullptr;
+  f->res_shift = nullptr;
+  f->res_cap = 0;
+  CS_CUDA(dalloc(&f->res_score, (size_t)R));
+  CS_CUDA(dalloc(&f->res_shift, (size_t)R * 3));
+  f->res_cap = R;
+  return CS_NGF_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void cs_ngf_default_config(cs_ngf_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->eps = 1e-5f;
+  cfg->gamma = 0.5f;
+}
+
+int32_t cs_ngf_auto_pad(int32_t n) { return (n >= 2 && n <= 256) ? auto_pad(n) : 0; }
+
+const char* cs_ngf_status_string(int32_t s) {
+  switch (s) {
+    case CS_NGF_OK: return "ok";
+    case CS_NGF_EINVAL: return "invalid argument";
+    case CS_NGF_ENOMEM: return "out of memory";
+    case CS_NGF_ECUDA: return "CUDA error";
+    case CS_NGF_ENOVALID: return "no valid shift for any rotation";
+    case CS_NGF_EUNSUPPORTED: return "unsupported size";
+    default: return "unknown status";
+  }
+}
+
+const char* cs_ngf_last_error(void) { return g_last_error.c_str(); }
+
+cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const int32_t dims[3],
+                                   const cs_ngf_config* cfg_in, void* stream, cs_ngf_fixed** out) {
+  g_last_error.clear();
+  if (!out) return fail(CS_NGF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A || !maskA || !dims) return fail(CS_NGF_EINVAL, "A, maskA or dims is NULL");
+  cs_ngf_config cfg;
+  cs_ngf_default_config(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 2 || dims[a] > 256)
+      return fail(CS_NGF_EINVAL, "dims must be in [2, 256], got " + std::to_string(dims[a]));
+  if (!(cfg.eps > 0.0f) || !std::isfinite(cfg.eps)) return fail(CS_NGF_EINVAL, "eps must be > 0");
+  if (!(cfg.gamma > 0.0f && cfg.gamma <= 1.0f)) return fail(CS_NGF_EINVAL, "gamma must be in (0, 1]");
+  if (cfg.batch < 0) return fail(CS_NGF_EINVAL, "batch must be >= 0");
+  int pad[3];
+  for (int a = 0; a < 3; ++a) {
+    pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
+    if (!pad_supported(pad[a]))
+      return fail(CS_NGF_EUNSUPPORTED, "FFT length " + std::to_string(pad[a]) + " not supported");
+    if (pad[a] < 2 * dims[a] - 1)
+      return fail(CS_NGF_EINVAL, "FFT length " + std::to_string(pad[a]) + " < 2n-1");
+  }
+
+  cs_ngf_fixed* f = new (std::nothrow) cs_ngf_fixed();
+  if (!f) return fail(CS_NGF_ENOMEM, "host allocation failed");
+  cudaGetDevice(&f->device);
+  f->eps = cfg.eps;
+  f->gamma = cfg.gamma;
+  Geo& g = f->g;
+  g.nz = dims[0]; g.ny = dims[1]; g.nx = dims[2];
+  g.Pz = pad[0]; g.Py = pad[1]; g.Px = pad[2];
+  g.vz = 2 * g.nz - 1; g.vy = 2 * g.ny - 1; g.vx = 2 * g.nx - 1;
+  g.eps2 = cfg.eps * cfg.eps;
+  g.nvox = (long long)g.nz * g.ny * g.nx;
+
+  const size_t f0 = (size_t)4 * g.nz * g.ny * g.Px, f2 = (size_t)g.vz * g.Px * g.Py;
+  const size_t f1 = (size_t)4 * g.nz * g.Px * g.Py, f3 = (size_t)g.vz * g.vy * g.Px;
+  f->f02_elems = std::max(f0, f2);
+  f->f13_elems = std::max(f1, f3);
+  const size_t per_rot = (f->f02_elems + f->f13_elems) * sizeof(float2) + (size_t)g.nvox * 5;
+  const size_t uv_elems = (size_t)7 * (g.Px / 2 + 1) * g.Py * g.Pz;
+  int batch = cfg.batch;
+  if (batch == 0) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t budget = free_b > uv_elems * sizeof(float2) ? (free_b - uv_elems * sizeof(float2)) / 3 : 0;
+    batch = (int)std::max<size_t>(1, std::min<size_t>(32, budget / per_rot));
+  }
+  f->batch = batch;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  auto bail = [&](cs_ngf_status s) { std::string m = g_last_error; free_handle(f); g_last_error = m; return s; };
+#define CS_TRY(call) do { cs_ngf_status s_ = (call); if (s_) return bail(s_); } while (0)
+#define CS_TRYC(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return bail(fail( \
+    e_ == cudaErrorMemoryAllocation ? CS_NGF_ENOMEM : CS_NGF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); } while (0)
+
+  CS_TRYC(dalloc(&f->UV, uv_elems));
+  CS_TRYC(dalloc(&f->Bh, (size_t)batch * g.nvox));
+  CS_TRYC(dalloc(&f->Mh, (size_t)batch * g.nvox));
+  CS_TRYC(dalloc(&f->F02, (size_t)batch * f->f02_elems));
+  CS_TRYC(dalloc(&f->F13, (size_t)batch * f->f13_elems));
+  CS_TRYC(dalloc(&f->msum, (size_t)batch));
+  CS_TRYC(dalloc(&f->thr, (size_t)batch));
+  CS_TRYC(dalloc(&f->keys, (size_t)batch));
+  f->fixed_bytes = uv_elems * sizeof(float2);
+  f->workspace_bytes = (size_t)batch * per_rot;
+  for (int a = 0; a < 3; ++a) {
+    f->tw[a] = nullptr;
+    for (int b = 0; b < a; ++b)
+      if (pad[b] == pad[a]) f->tw[a] = f->tw[b];
+    if (!f->tw[a]) CS_TRY(make_twiddles(pad[a], &f->tw[a]));
+  }
+
+  // A side into the new handle
+  CS_TRY(run_fixed(f, A, maskA, st));
+#undef CS_TRY
+#undef CS_TRYC
+  *out = f;
+  return CS_NGF_OK;
+}
+
+cs_ngf_status cs_ngf_score_rotations(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                                     const double* quats, int32_t R, float* best_score,
+                                     int32_t* best_shift, void* stream) {
+  g_last_error.clear();
+  if (cs_ngf_status s = check_volume_args(f, B, maskB)) return s;
+  DeviceGuard guard(f->device);
+  return score_all(f, B, maskB, quats, R, best_score, best_shift, (cudaStream_t)stream);
+}
+
+cs_ngf_status cs_ngf_score_rotations_host(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                                          const double* quats, int32_t R, float* best_score,
+                                          int32_t* best_shift, void* stream) {
+  g_last_error.clear();
+  if (cs_ngf_status s = check_volume_args(f, B, maskB)) return s;
+  if (!best_score || !best_shift) return fail(CS_NGF_EINVAL, "output pointer is NULL");
+  if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
+  DeviceGuard guard(f->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!f->stage_B) {
+    CS_CUDA(dalloc(&f->stage_B, (size_t)f->g.nvox));
+    CS_CUDA(dalloc(&f->stage_M, (size_t)f->g.nvox));
+  }
+  if (cs_ngf_status s = ensure_results(f, R)) return s;
+  CS_CUDA(cudaMemcpyAsync(f->stage_B, B, sizeof(float) * f->g.nvox, cudaMemcpyHostToDevice, st));
+  CS_CUDA(cudaMemcpyAsync(f->stage_M, maskB, (size_t)f->g.nvox, cudaMemcpyHostToDevice, st));
+  if (cs_ngf_status s = score_all(f, f->stage_B, f->stage_M, quats, R, f->res_score, f->res_shift, st))
+    return s;
+  CS_CUDA(cudaMemcpyAsync(best_score, f->res_score, sizeof(float) * R, cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaMemcpyAsync(best_shift, f->res_shift, sizeof(int32_t) * 3 * R, cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaStreamSynchronize(st));
+  return CS_NGF_OK;
+}
+
+cs_ngf_status cs_ngf_align(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                           const double* quats, int32_t R, float* score, int32_t* rot_index,
+                           int32_t shift[3], void* stream) {
+  g_last_error.clear();
+  if (cs_ngf_status s = check_volume_args(f, B, maskB)) return s;
+  if (!score || !rot_index || !shift) return fail(CS_NGF_EINVAL, "output pointer is NULL");
+  if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
+  DeviceGuard guard(f->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cs_ngf_status s = ensure_results(f, R)) return s;
+  if (cs_ngf_status s = score_all(f, B, maskB, quats, R, f->res_score, f->res_shift, st)) return s;
+  std::vector<float> sc(R);
+  std::vector<int32_t> sh(3 * (size_t)R);
+  CS_CUDA(cudaMemcpyAsync(sc.data(), f->res_score, sizeof(float) * R, cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaMemcpyAsync(sh.data(), f->res_shift, sizeof(int32_t) * 3 * R, cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaStreamSynchronize(st));
+  int best = -1;
+  for (int r = 0; r < R; ++r)
+    if (std::isfinite(sc[r]) && (best < 0 || sc[r] > sc[best])) best = r;
+  if (best < 0) {
+    *score = -INFINITY;
+    *rot_index = -1;
+    shift[0] = shift[1] = shift[2] = 0;
+    return fail(CS_NGF_ENOVALID, "no rotation has a valid shift");
+  }
+  *score = sc[best];
+  *rot_index = best;
+  for (int a = 0; a < 3; ++a) shift[a] = sh[3 * (size_t)best + a];
+  return CS_NGF_OK;
+}
+
+cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                               const double* quat, float* map, void* stream) {
+  g_last_error.clear();
+  if (cs_ngf_status s = check_volume_args(f, B, maskB)) return s;
+  if (!map) return fail(CS_NGF_EINVAL, "map is NULL");
+  DeviceGuard guard(f->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cs_ngf_status s = ensure_results(f, 1)) return s;
+  if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
+  return score_batch(f, B, maskB, 0, 1, f->res_score, f->res_shift, map, st);
+}
+
+cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
+                              const double* quat, float* Bhat, uint8_t* Mhat, void* stream) {
+  g_last_error.clear();
+  if (cs_ngf_status s = check_volume_args(f, B, maskB)) return s;
+  if (!Bhat || !Mhat) return fail(CS_NGF_EINVAL, "output pointer is NULL");
+  DeviceGuard guard(f->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
+  CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
+  const Geo& g = f->g;
+  k_resample<<<dim3((unsigned)(g.nz * g.ny), 1u), 128, 0, st>>>(B, maskB, f->rot_d, g, Bhat, Mhat, f->msum);
+  return check_launch("resample");
+}
+
+cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info) {
+  if (!f || !info) return fail(CS_NGF_EINVAL, "handle or info is NULL");
+  info->dims[0] = f->g.nz; info->dims[1] = f->g.ny; info->dims[2] = f->g.nx;
+  info->pad[0] = f->g.Pz; info->pad[1] = f->g.Py; info->pad[2] = f->g.Px;
+  info->batch = f->batch;
+  info->sum_mask_a = f->sumA;
+  info->fixed_bytes = (int64_t)f->fixed_bytes;
+  info->workspace_bytes = (int64_t)f->workspace_bytes;
+  return CS_NGF_OK;
+}
+
+void cs_ngf_release(cs_ngf_fixed* f) { free_handle(f); }
+
+cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* maskA, void* stream) {
+  g_last_error.clear();
+  if (!f) return fail(CS_NGF_EINVAL, "handle is NULL");
+  if (!A || !maskA) return fail(CS_NGF_EINVAL, "A or maskA is NULL");
+  DeviceGuard guard(f->device);
+  return run_fixed(f, A, maskA, (cudaStream_t)stream);
+}
+
+cs_ngf_status cs_ngf_set_profiling(cs_ngf_fixed* f, int32_t on) {
+  if (!f) return fail(CS_NGF_EINVAL, "handle is NULL");
+  f->profiling = on != 0;
+  return CS_NGF_OK;
+}
+
+cs_ngf_status cs_ngf_stage_times(cs_ngf_fixed* f, double* ms, int64_t* launches) {
+  if (!f || !ms || !launches) return fail(CS_NGF_EINVAL, "NULL argument");
+  DeviceGuard guard(f->device);
+  for (int i = 0; i < CS_NGF_NSTAGES; ++i) { ms[i] = 0.0; launches[i] = 0; }
+  cs_ngf_status st = CS_NGF_OK;
+  for (auto& sp : f->spans) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(sp.b) != cudaSuccess || cudaEventElapsedTime(&t, sp.a, sp.b) != cudaSuccess)
+      st = fail(CS_NGF_ECUDA, "event timing failed");
+    if (sp.stage >= 0 && sp.stage < CS_NGF_NSTAGES) { ms[sp.stage] += t; launches[sp.stage] += 1; }
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  f->spans.clear();
+  return st;
+}
+
+int64_t cs_ngf_launch_count(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Element-wise kernels: trilinear rotate-resample with the rotated mask
+// (Section 3.2), mask sums, overlap thresholds and result decoding.
+#include "kernels.cuh"
+
+namespace csngf {
+
+namespace {
+struct AxisSample {
+  bool inside;
+  int i0;
+  float t;
+};
+
+// domain test, clamped base index and fraction for one axis (FP32, no contraction)
+__device__ __forceinline__ AxisSample axis_sample(float p, int n) {
+  AxisSample a;
+  const float slack = 1e-4f;
+  const float hi = __fadd_rn((float)(n - 1), slack);
+  a.inside = (p >= -slack) && (p <= hi);
+  float pc = fminf(fmaxf(p, 0.0f), (float)(n - 1));
+  int i0 = (int)floorf(pc);
+  i0 = min(i0, n - 2);
+  a.i0 = i0;
+  a.t = __fsub_rn(pc, (float)i0);
+  return a;
+}
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) {
+  return __fadd_rn(a, __fmul_rn(t, __fsub_rn(b, a)));
+}
+}  // namespace
+
+__global__ void k_resample(const float* __restrict__ B, const uint8_t* __restrict__ MB,
+                           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
+                           uint8_t* __restrict__ Mh, int* __restrict__ msum) {
+  const int r = blockIdx.y;
+  const int row = blockIdx.x;                 // z * ny + y
+  const int z = row / g.ny, y = row - z * g.ny;
+  const RotMat R = rot[r];
+  const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1), cz = 0.5f * (float)(g.nz - 1);
+  const float dy = __fsub_rn((float)y, cy), dz = __fsub_rn((float)z, cz);
+  int count = 0;
+  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+    const float dx = __fsub_rn((float)x, cx);
+    float p[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float acc = __fmul_rn(R.m[3 * i + 0], dx);
+      acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 1], dy));
+      acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 2], dz));
+      p[i] = __fadd_rn(acc, i == 0 ? cx : (i == 1 ? cy : cz));
+    }
+    AxisSample ax = axis_sample(p[0], g.nx), ay = axis_sample(p[1], g.ny), az = axis_sample(p[2], g.nz);
+    float val = 0.0f;
+    uint8_t m = 0;
+    if (ax.inside && ay.inside && az.inside) {
+      const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+      const long long b000 = (long long)az.i0 * sz + (long long)ay.i0 * sy + ax.i0;
+      const long long o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+      float v[8], mk[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        v[k] = __ldg(&B[b000 + o[k]]);
+        mk[k] = (float)__ldg(&MB[b000 + o[k]]);
+      }
+      // intensity: lerps along x, y, z (contraction allowed)
+      float v00 = v[0] + ax.t * (v[1] - v[0]), v01 = v[2] + ax.t * (v[3] - v[2]);
+      float v10 = v[4] + ax.t * (v[5] - v[4]), v11 = v[6] + ax.t * (v[7] - v[6]);
+      float v0 = v00 + ay.t * (v01 - v00), v1 = v10 + ay.t * (v11 - v10);
+      val = v0 + az.t * (v1 - v0);
+      // mask decision: same lerp order, round-to-nearest, no contraction
+      float m00 = lerp_rn(mk[0], mk[1], ax.t), m01 = lerp_rn(mk[2], mk[3], ax.t);
+      float m10 = lerp_rn(mk[4], mk[5], ax.t), m11 = lerp_rn(mk[6], mk[7], ax.t);
+      float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
+      float mm = lerp_rn(m0, m1, az.t);
+      m = (mm >= 0.5f) ? 1 : 0;
+    }
+    const long long idx = (long long)r * g.nvox + (long long)row * g.nx + x;
+    Bh[idx] = val;
+    Mh[idx] = m;
+    count += m;
+  }
+  // block reduction of the mask count
+  for (int off = 16; off > 0; off >>= 1) count += __shfl_down_sync(0xffffffffu, count, off);
+  __shared__ int warp_sums[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_sums[wid] = count;
+  __syncthreads();
+  if (wid == 0) {
+    int c = (lane < (int)((blockDim.x + 31) >> 5)) ? warp_sums[lane] : 0;
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+    if (lane == 0 && c) atomicAdd(&msum[r], c);
+  }
+}
+
+__global__ void k_mask_sum(const uint8_t* __restrict__ M, long long n, int* __restrict__ out) {
+  int c = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    c += M[i] ? 1 : 0;
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+__global__ void k_thresholds(const int* __restrict__ msumB, int sumA, float gamma, double pvol,
+                             int nrot, float* __restrict__ thr) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrot) return;
+  const int mn = min(sumA, msumB[r]);
+  double t = ceil((double)gamma * (double)mn);
+  if (t < 1.0) t = 1.0;
+  thr[r] = (float)((t - 0.5) * pvol);
+}
+
+__global__ void k_finalize(const unsigned long long* __restrict__ keys, int nrot, Geo g,
+                           float* __restrict__ best_score, int32_t* __restrict__ best_shift) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrot) return;
+  const unsigned long long k = keys[r];
+  if (k == 0ull) {
+    best_score[r] = __int_as_float(0xff800000);   // -inf: no valid shift
+    best_shift[3 * r + 0] = 0;
+    best_shift[3 * r + 1] = 0;
+    best_shift[3 * r + 2] = 0;
+    return;
+  }
+  unsigned u = (unsigned)(k >> 32);
+  u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  const unsigned lin = 0xFFFFFFFFu - (unsigned)(k & 0xFFFFFFFFull);
+  const int vx = (int)(lin % (unsigned)g.vx);
+  const int vy = (int)((lin / (unsigned)g.vx) % (unsigned)g.vy);
+  const int vz = (int)(lin / ((unsigned)g.vx * (unsigned)g.vy));
+  best_score[r] = __uint_as_float(u);
+  best_shift[3 * r + 0] = vz - (g.nz - 1);
+  best_shift[3 * r + 1] = vy - (g.ny - 1);
+  best_shift[3 * r + 2] = vx - (g.nx - 1);
+}
+
+__global__ void k_copy_in(const float* __restrict__ A, const uint8_t* __restrict__ MA, long long n,
+                          float* __restrict__ Bh, uint8_t* __restrict__ Mh) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    Bh[i] = A[i];
+    Mh[i] = MA[i] ? 1 : 0;
+  }
+}
+
+}  // namespace csngf

@@ -1,0 +1,230 @@
+// Register-level DFTs and the two-level (four-step) block FFT used by every
+// transform pass of the all-shift NGF correlation (Eq. 7-8: the channel and
+// mask correlations are evaluated in the frequency domain).
+//
+// Conventions: forward transforms use S = -1, X[k] = sum_n x[n] exp(-2 pi i nk/N);
+// inverse transforms use S = +1 and are unnormalised.
+//
+// A length N = N1 * N2 transform is split as n = N2*n1 + n2, k = k1 + N1*k2:
+//   step 1: for each n2, an N1-point DFT over n1 in registers, then the
+//           twiddle exp(S 2 pi i n2 k1 / N), then a store to shared memory;
+//   step 2: for each k1, an N2-point DFT over n2 in registers; its k2-th
+//           output is X[k1 + N1*k2].
+// One shared-memory exchange per transform; the caller decides where the
+// step-1 inputs come from and where the step-2 outputs go.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <utility>
+#include <type_traits>
+
+namespace csngf {
+
+// ---------------------------------------------------------------- twiddles
+// Compile-time cos/sin of 2*pi*e/R from their Maclaurin series after an exact
+// quadrant reduction done in integers, so quarter-turn twiddles are exact.
+namespace ctw {
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double sin_series(double a) {
+  double a2 = a * a, term = a, sum = a;
+  for (int k = 1; k <= 14; ++k) { term *= -a2 / ((2.0 * k) * (2.0 * k + 1.0)); sum += term; }
+  return sum;
+}
+constexpr double cos_series(double a) {
+  double a2 = a * a, term = 1.0, sum = 1.0;
+  for (int k = 1; k <= 14; ++k) { term *= -a2 / ((2.0 * k - 1.0) * (2.0 * k)); sum += term; }
+  return sum;
+}
+// angle = 2*pi*e/R = q*(pi/2) + (pi/2)*rem/R with rem in [0, R)
+constexpr double cos2pi(long e, long R) {
+  e %= R; if (e < 0) e += R;
+  long q = (4 * e) / R, rem = 4 * e - q * R;
+  double a = (kPi / 2.0) * (double)rem / (double)R;
+  double c = cos_series(a), s = sin_series(a);
+  return (q & 3) == 0 ? c : (q & 3) == 1 ? -s : (q & 3) == 2 ? -c : s;
+}
+constexpr double sin2pi(long e, long R) {
+  e %= R; if (e < 0) e += R;
+  long q = (4 * e) / R, rem = 4 * e - q * R;
+  double a = (kPi / 2.0) * (double)rem / (double)R;
+  double c = cos_series(a), s = sin_series(a);
+  return (q & 3) == 0 ? s : (q & 3) == 1 ? c : (q & 3) == 2 ? -s : -c;
+}
+}  // namespace ctw
+
+// ---------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a * (S i)
+template <int S>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+  return S < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// static for-loop with compile-time index
+template <class F, int... I>
+__device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// multiply by exp(S 2 pi i E / R), E a compile-time constant
+template <int R, int S, int E>
+__device__ __forceinline__ float2 tw_mul(float2 x) {
+  constexpr int e = ((E % R) + R) % R;
+  if constexpr (e == 0) {
+    return x;
+  } else if constexpr (2 * e == R) {
+    return make_float2(-x.x, -x.y);
+  } else if constexpr (4 * e == R) {
+    return mul_si<S>(x);
+  } else if constexpr (4 * e == 3 * R) {
+    return mul_si<-S>(x);
+  } else {
+    constexpr float c = (float)ctw::cos2pi(e, R);
+    constexpr float s = (float)(S * ctw::sin2pi(e, R));
+    return make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
+  }
+}
+
+// ---------------------------------------------------------------- DFTs
+template <int R, int S>
+struct Dft;
+
+template <int S>
+struct Dft<1, S> {
+  __device__ __forceinline__ static void run(float2 (&)[1]) {}
+};
+
+template <int S>
+struct Dft<2, S> {
+  __device__ __forceinline__ static void run(float2 (&v)[2]) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <int S>
+struct Dft<4, S> {
+  __device__ __forceinline__ static void run(float2 (&v)[4]) {
+    float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    float2 b0 = cadd(v[1], v[3]), b1 = mul_si<S>(csub(v[1], v[3]));
+    v[0] = cadd(a0, b0);
+    v[2] = csub(a0, b0);
+    v[1] = cadd(a1, b1);
+    v[3] = csub(a1, b1);
+  }
+};
+
+template <int S>
+struct Dft<5, S> {
+  __device__ __forceinline__ static void run(float2 (&v)[5]) {
+    constexpr float c1 = (float)ctw::cos2pi(1, 5), c2 = (float)ctw::cos2pi(2, 5);
+    constexpr float s1 = (float)ctw::sin2pi(1, 5), s2 = (float)ctw::sin2pi(2, 5);
+    float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+    float2 x0 = v[0];
+    v[0] = cadd(x0, cadd(t1, t2));
+    float2 a1 = make_float2(x0.x + c1 * t1.x + c2 * t2.x, x0.y + c1 * t1.y + c2 * t2.y);
+    float2 a2 = make_float2(x0.x + c2 * t1.x + c1 * t2.x, x0.y + c2 * t1.y + c1 * t2.y);
+    float2 b1 = make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+    float2 b2 = make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+    // forward: X1 = a1 - i b1, X4 = a1 + i b1, X2 = a2 - i b2, X3 = a2 + i b2
+    float2 ib1 = mul_si<S>(b1), ib2 = mul_si<S>(b2);   // S i b
+    v[1] = cadd(a1, ib1);
+    v[4] = csub(a1, ib1);
+    v[2] = cadd(a2, ib2);
+    v[3] = csub(a2, ib2);
+  }
+};
+
+constexpr int first_factor(int R) {
+  return (R % 4 == 0 && R != 4) ? 4 : (R % 2 == 0 && R != 2) ? 2 : (R % 5 == 0 && R != 5) ? 5 : R;
+}
+
+// composite R = A * B in registers (same split as the block four-step)
+template <int R, int S>
+struct Dft {
+  static constexpr int A = first_factor(R);
+  static constexpr int B = R / A;
+  static_assert(A * B == R && A > 1 && B > 1, "unsupported DFT length");
+  __device__ __forceinline__ static void run(float2 (&v)[R]) {
+    float2 t[B][A];
+    sfor<B>([&](auto bc) {
+      constexpr int b = decltype(bc)::value;
+      float2 s[A];
+      sfor<A>([&](auto ac) { constexpr int a = decltype(ac)::value; s[a] = v[B * a + b]; });
+      Dft<A, S>::run(s);
+      sfor<A>([&](auto kc) {
+        constexpr int ka = decltype(kc)::value;
+        t[b][ka] = tw_mul<R, S, b * ka>(s[ka]);
+      });
+    });
+    sfor<A>([&](auto kc) {
+      constexpr int ka = decltype(kc)::value;
+      float2 u[B];
+      sfor<B>([&](auto bc) { constexpr int b = decltype(bc)::value; u[b] = t[b][ka]; });
+      Dft<B, S>::run(u);
+      sfor<B>([&](auto kb) { constexpr int k = decltype(kb)::value; v[ka + A * k] = u[k]; });
+    });
+  }
+};
+
+// ---------------------------------------------------------------- four-step
+template <int N>
+struct Split;   // N = N1 * N2 with N1 <= N2 (step 2 then has at most one item per thread)
+template <> struct Split<16>  { static constexpr int N1 = 4,  N2 = 4; };
+template <> struct Split<32>  { static constexpr int N1 = 4,  N2 = 8; };
+template <> struct Split<64>  { static constexpr int N1 = 8,  N2 = 8; };
+template <> struct Split<128> { static constexpr int N1 = 8,  N2 = 16; };
+template <> struct Split<160> { static constexpr int N1 = 8,  N2 = 20; };
+template <> struct Split<200> { static constexpr int N1 = 8,  N2 = 25; };
+template <> struct Split<256> { static constexpr int N1 = 16, N2 = 16; };
+template <> struct Split<320> { static constexpr int N1 = 16, N2 = 20; };
+template <> struct Split<400> { static constexpr int N1 = 16, N2 = 25; };
+template <> struct Split<512> { static constexpr int N1 = 16, N2 = 32; };
+
+template <int N>
+struct FourStep {
+  static constexpr int N1 = Split<N>::N1;
+  static constexpr int N2 = Split<N>::N2;
+  // exchange layout per sequence: [n2][k1] with padded strides (odd strides keep
+  // 16 consecutive lanes on distinct bank pairs for either lane ordering)
+  static constexpr int RS = (N1 % 2 == 0) ? N1 + 1 : N1;
+  static constexpr int CS0 = N2 * RS;
+  static constexpr int CS = (CS0 % 2 == 0) ? CS0 + 1 : CS0;
+  static_assert(CS >= N, "sequence stride must hold N natural-order values");
+
+  // v holds x[N2*n1 + n2] for n1 = 0..N1-1; writes twiddled N1-point outputs
+  template <int S>
+  __device__ __forceinline__ static void step1(float2 (&v)[N1], float2* ex_seq, int n2,
+                                               const float2* __restrict__ twN) {
+    Dft<N1, S>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      float2 w = __ldg(&twN[n2 * k1]);
+      if (S > 0) w.y = -w.y;
+      ex_seq[n2 * RS + k1] = (k1 == 0) ? v[k1] : cmul(v[k1], w);
+    }
+  }
+
+  // u[k2] = X[k1 + N1*k2]
+  template <int S>
+  __device__ __forceinline__ static void step2(float2 (&u)[N2], const float2* ex_seq, int k1) {
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) u[n2] = ex_seq[n2 * RS + k1];
+    Dft<N2, S>::run(u);
+  }
+};
+
+}  // namespace csngf

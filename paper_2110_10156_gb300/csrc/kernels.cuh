@@ -1,0 +1,89 @@
+// Kernels of the all-shift NGF correlation hot path (Cross-Sim-NGF,
+// Sections 3.1-3.2).  Per rotation of the floating volume B:
+//
+//   resample   B_hat = B o T_theta (trilinear) and the rotated mask    (Sec. 3.2)
+//   fwd_x      NGF of B_hat (Eq. 1), the six Eq. 6 channels and the mask,
+//              packed as four complex fields, x-axis FFT
+//   fwd_y      y-axis FFT
+//   zmac       z-axis FFT, the spectral multiply-accumulate against the
+//              fixed volume's spectra (Eq. 7-8, summed before the inverse),
+//              z-axis inverse FFT of X + iY (numerator and overlap count)
+//   inv_y      y-axis inverse FFT
+//   inv_x      x-axis inverse FFT, s = X / N over the valid shifts (Eq. 5,
+//              minimum overlap gamma), per-rotation argmax
+//
+// Data layout (all [slow]...[fast], complex64 = float2):
+//   Bh, Mh   [r][z][y][x]                     float / uint8
+//   F0       [r][j][z][y][kx]     j < 4        x transformed
+//   F1       [r][j][z][kx][ky]                  x, y transformed
+//   F2       [r][vz][kx][ky]                    Z = X + iY after the z inverse
+//   F3       [r][vz][vy][kx]                    after the y inverse
+//   UV       [7][kx <= Px/2][ky][kz]           fixed-volume weights (prepare)
+// vz, vy, vx index the shift chi = v - (n - 1) in [-(n-1), n-1].
+//
+// Packed channel pairs: j=0 (xx, yy), j=1 (zz, xy), j=2 (xz, yz), j=3 (mask, 0).
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace csngf {
+
+struct Geo {
+  int nz, ny, nx;       // volume dims
+  int Pz, Py, Px;       // FFT lengths per axis
+  int vz, vy, vx;       // 2n - 1 shift extents
+  float eps2;           // eps^2 (Eq. 1)
+  long long nvox;       // nz*ny*nx
+};
+
+// per-rotation matrix (row-major, acts on (x, y, z)), rounded to FP32 on the host
+struct RotMat { float m[9]; };
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// orderable key: larger score -> larger key; equal score -> smaller index wins
+__device__ __forceinline__ unsigned long long make_key(float s, unsigned lin) {
+  unsigned u = __float_as_uint(s);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 32) | (unsigned long long)(0xFFFFFFFFu - lin);
+}
+
+// ----------------------------------------------------------------- resample
+// Section 3.2: B_hat(x) = B(R (x - c) + c), trilinear; the rotated mask is
+// [trilinear M_B >= 0.5] inside [0, n-1]^3 (+-1e-4).  The sample point and the
+// mask decision use round-to-nearest FP32 operations in a fixed order (no
+// contraction), so the decision is reproducible bit for bit.
+__global__ void k_resample(const float* __restrict__ B, const uint8_t* __restrict__ MB,
+                           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
+                           uint8_t* __restrict__ Mh, int* __restrict__ msum);
+
+// sum of a uint8 mask (for the fixed volume)
+__global__ void k_mask_sum(const uint8_t* __restrict__ M, long long n, int* __restrict__ out);
+
+// per-rotation overlap threshold in FFT units: (max(1, ceil(gamma min(sA, sB))) - 0.5) * Pz Py Px
+__global__ void k_thresholds(const int* __restrict__ msumB, int sumA, float gamma, double pvol,
+                             int nrot, float* __restrict__ thr);
+
+// decode per-rotation keys into (score, shift)
+__global__ void k_finalize(const unsigned long long* __restrict__ keys, int nrot, Geo g,
+                           float* __restrict__ best_score, int32_t* __restrict__ best_shift);
+
+// copy a float volume / mask into the rotation-0 slot (fixed-volume prepare)
+__global__ void k_copy_in(const float* __restrict__ A, const uint8_t* __restrict__ MA,
+                          long long n, float* __restrict__ Bh, uint8_t* __restrict__ Mh);
+
+// ----------------------------------------------------------------- FFT passes
+template <int P> void launch_fwd_x(const float* Bh, const uint8_t* Mh, float2* F0, const float2* tw,
+                                   Geo g, int nrot, cudaStream_t st);
+template <int P> void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nrot,
+                                   cudaStream_t st);
+template <int P> void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw,
+                                  Geo g, int nrot, cudaStream_t st);
+template <int P> void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g,
+                                    cudaStream_t st);
+template <int P> void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nrot,
+                                   cudaStream_t st);
+template <int P> void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys,
+                                   float* map, const float2* tw, Geo g, int nrot, cudaStream_t st);
+
+}  // namespace csngf

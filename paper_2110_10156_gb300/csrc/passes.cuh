@@ -1,0 +1,524 @@
+// FFT passes of the all-shift NGF correlation (Cross-Sim-NGF Eq. 6-8).
+// Included by one translation unit per FFT length (passes_<P>.cu).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace csngf {
+
+// output index m of a length-P transform -> shift slot v = chi + n - 1, or -1
+__device__ __forceinline__ int shift_slot(int m, int n, int P) {
+  if (m <= n - 1) return m + n - 1;
+  if (m >= P - (n - 1)) return m - P + n - 1;
+  return -1;
+}
+
+template <class K>
+static void set_smem(K kern, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// fwd_x: Eq. 1 NGF of the resampled volume, the Eq. 6 channels packed in four
+// complex fields, and the x-axis FFT of every row (zero padded to Px).
+// Block: ROWS rows of one slab; thread (row, n2) gathers x = N2*n1 + n2.
+// ---------------------------------------------------------------------------
+template <int P, int ROWS>
+__global__ void __launch_bounds__(ROWS * Split<P>::N2)
+k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __restrict__ F0,
+        const float2* __restrict__ tw, Geo g, long long nrows) {
+  using FS = FourStep<P>;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
+  extern __shared__ float2 ex[];
+  const int t = threadIdx.x;
+  const int lrow = t / N2, n2 = t - lrow * N2;
+  const long long grow = (long long)blockIdx.x * ROWS + lrow;
+  const bool row_ok = grow < nrows;
+  const long long rz = row_ok ? grow / g.ny : 0;
+  const int y = row_ok ? (int)(grow - rz * g.ny) : 0;
+  const int r = (int)(rz / g.nz), z = (int)(rz - (long long)r * g.nz);
+
+  float vx[N1], vy[N1], vz[N1], mm[N1];
+  const float* V = Bh + (long long)r * g.nvox;
+  const uint8_t* M = Mh + (long long)r * g.nvox;
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  const int ym = max(y - 1, 0), yp = min(y + 1, g.ny - 1);
+  const int zm = max(z - 1, 0), zp = min(z + 1, g.nz - 1);
+  const long long base = (long long)z * sz + (long long)y * sy;
+#pragma unroll
+  for (int n1 = 0; n1 < N1; ++n1) {
+    const int x = N2 * n1 + n2;
+    vx[n1] = vy[n1] = vz[n1] = mm[n1] = 0.0f;
+    if (row_ok && x < g.nx) {
+      const int xm = max(x - 1, 0), xp = min(x + 1, g.nx - 1);
+      const float gx = 0.5f * (__ldg(&V[base + xp]) - __ldg(&V[base + xm]));
+      const float gy = 0.5f * (__ldg(&V[(long long)z * sz + (long long)yp * sy + x]) -
+                               __ldg(&V[(long long)z * sz + (long long)ym * sy + x]));
+      const float gz = 0.5f * (__ldg(&V[(long long)zp * sz + (long long)y * sy + x]) -
+                               __ldg(&V[(long long)zm * sz + (long long)y * sy + x]));
+      const float inv = rsqrtf(gx * gx + gy * gy + gz * gz + g.eps2);
+      vx[n1] = gx * inv;
+      vy[n1] = gy * inv;
+      vz[n1] = gz * inv;
+      mm[n1] = M[base + x] ? 1.0f : 0.0f;
+    }
+  }
+  const long long rows_per_field = (long long)g.nz * g.ny;
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const float m = mm[n1];
+      switch (j) {
+        case 0: v[n1] = make_float2(m * vx[n1] * vx[n1], m * vy[n1] * vy[n1]); break;
+        case 1: v[n1] = make_float2(m * vz[n1] * vz[n1], m * vx[n1] * vy[n1]); break;
+        case 2: v[n1] = make_float2(m * vx[n1] * vz[n1], m * vy[n1] * vz[n1]); break;
+        default: v[n1] = make_float2(m, 0.0f); break;
+      }
+    }
+    FS::template step1<-1>(v, ex + lrow * CS, n2, tw);
+    __syncthreads();
+    if (t < ROWS * N1) {
+      const int lr = t / N1, k1 = t - lr * N1;
+      const long long gr = (long long)blockIdx.x * ROWS + lr;
+      if (gr < nrows) {
+        float2 u[N2];
+        FS::template step2<-1>(u, ex + lr * CS, k1);
+        const long long rz2 = gr / g.ny;
+        const int y2 = (int)(gr - rz2 * g.ny);
+        const int r2 = (int)(rz2 / g.nz), z2 = (int)(rz2 - (long long)r2 * g.nz);
+        float2* dst = F0 + ((((long long)r2 * 4 + j) * rows_per_field + (long long)z2 * g.ny + y2) * P);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int P>
+void launch_fwd_x(const float* Bh, const uint8_t* Mh, float2* F0, const float2* tw, Geo g, int nrot,
+                  cudaStream_t st) {
+  constexpr int N2 = Split<P>::N2;
+  constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
+  const long long nrows = (long long)nrot * g.nz * g.ny;
+  const size_t smem = (size_t)ROWS * FourStep<P>::CS * sizeof(float2);
+  set_smem(k_fwd_x<P, ROWS>, smem);
+  const unsigned blocks = (unsigned)((nrows + ROWS - 1) / ROWS);
+  k_fwd_x<P, ROWS><<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
+}
+
+// ---------------------------------------------------------------------------
+// fwd_y: y-axis FFT of every column of F0 (rows y >= ny are zero); the output
+// is transposed so that ky is contiguous for the z pass.
+// Block: W consecutive kx of one (r, j, z) plane.
+// ---------------------------------------------------------------------------
+template <int P, int W>
+__global__ void __launch_bounds__(W * Split<P>::N2)
+k_fwd_y(const float2* __restrict__ F0, float2* __restrict__ F1, const float2* __restrict__ tw,
+        Geo g) {
+  using FS = FourStep<P>;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
+  extern __shared__ float2 ex[];
+  const int t = threadIdx.x;
+  const long long plane = blockIdx.x;
+  const int kx0 = blockIdx.y * W;
+  {
+    const int col = t % W, n2 = t / W;
+    const int kx = kx0 + col;
+    const float2* src = F0 + plane * (long long)g.ny * g.Px;
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const int y = N2 * n1 + n2;
+      v[n1] = (y < g.ny && kx < g.Px) ? src[(long long)y * g.Px + kx] : make_float2(0.f, 0.f);
+    }
+    FS::template step1<-1>(v, ex + col * CS, n2, tw);
+  }
+  __syncthreads();
+  if (t < W * N1) {
+    const int col = t / N1, k1 = t - col * N1;
+    const int kx = kx0 + col;
+    if (kx < g.Px) {
+      float2 u[N2];
+      FS::template step2<-1>(u, ex + col * CS, k1);
+      float2* dst = F1 + (plane * g.Px + kx) * (long long)P;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
+    }
+  }
+}
+
+template <int P>
+void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nrot, cudaStream_t st) {
+  constexpr int W = 16, N2 = Split<P>::N2;
+  const size_t smem = (size_t)W * FourStep<P>::CS * sizeof(float2);
+  set_smem(k_fwd_y<P, W>, smem);
+  dim3 grid((unsigned)(nrot * 4 * g.nz), (unsigned)((g.Px + W - 1) / W));
+  k_fwd_y<P, W><<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
+}
+
+// ---------------------------------------------------------------------------
+// zmac: for W columns (kx, ky) and their mirrors (-kx, -ky):
+//   z-axis FFT of the four packed fields,
+//   X(k) = sum_j U_j(k) H_j(k) + V_j(k) conj(H_j(-k))   (six weighted channels)
+//   Y(k) = U_3(k) H_3(k)                                 (mask correlation)
+//   z-axis inverse FFT of Z = X + iY at k and of conj(X) + i conj(Y) at -k,
+// keeping the 2nz-1 shift planes.  Loops over the batch's rotations so the
+// fixed spectra tile stays in L2.
+// ---------------------------------------------------------------------------
+template <int P, int W>
+__global__ void __launch_bounds__(2 * W * Split<P>::N2)
+k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
+       const float2* __restrict__ tw, Geo g, int nrot) {
+  using FS = FourStep<P>;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
+  constexpr int NC = 2 * W, NT = NC * N2, MI = (W * P + NT - 1) / NT;
+  extern __shared__ float2 ex[];
+  const int t = threadIdx.x;
+  const int kx = blockIdx.y, ky0 = blockIdx.x * W;
+  const int mkx = (g.Px - kx) % g.Px;
+  const bool self_mirror = (2 * kx) % g.Px == 0;
+  const long long hx = g.Px / 2 + 1;
+  const long long S7 = hx * g.Py * (long long)P;
+
+  // step-1 role: column c1 (fastest), n2
+  const int c1 = t % NC, n2 = t / NC;
+  const int pk1 = ky0 + (c1 < W ? c1 : c1 - W);
+  const bool ok1 = pk1 < g.Py;
+  const int ky1 = c1 < W ? pk1 : (g.Py - pk1) % g.Py;
+  const int kx1 = c1 < W ? kx : mkx;
+  // step-2 role: column c2 (fastest), k1
+  const bool has2 = t < NC * N1;
+  const int c2 = t % NC, k1 = t / NC;
+  const long long plane_stride = (long long)g.Px * g.Py;
+
+  for (int r = 0; r < nrot; ++r) {
+    float2 X[MI], Y[MI];
+#pragma unroll
+    for (int m = 0; m < MI; ++m) X[m] = Y[m] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      const float2* src = F1 + ((long long)r * 4 + j) * g.nz * plane_stride;
+      float2 v[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) {
+        const int z = N2 * n1 + n2;
+        v[n1] = (ok1 && z < g.nz) ? src[(long long)z * plane_stride + (long long)kx1 * g.Py + ky1]
+                                  : make_float2(0.f, 0.f);
+      }
+      FS::template step1<-1>(v, ex + c1 * CS, n2, tw);
+      __syncthreads();
+      float2 u[N2];
+      if (has2) FS::template step2<-1>(u, ex + c2 * CS, k1);
+      __syncthreads();
+      if (has2) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) ex[c2 * CS + k1 + N1 * k2] = u[k2];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < MI; ++m) {
+        const int i = t + NT * m;
+        if (i < W * P) {
+          const int c = i / P, kz = i - c * P;
+          const int ky = ky0 + c;
+          if (ky < g.Py) {
+            const float2 h = ex[c * CS + kz];
+            const long long o = ((long long)kx * g.Py + ky) * P + kz;
+            if (j < 3) {
+              const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
+              const float2 U = __ldg(&UV[(2 * j) * S7 + o]);
+              const float2 V = __ldg(&UV[(2 * j + 1) * S7 + o]);
+              X[m] = cadd(X[m], cadd(cmul(U, h), cmul(V, hm)));
+            } else {
+              const float2 U = __ldg(&UV[6 * S7 + o]);
+              Y[m] = cadd(Y[m], cmul(U, h));
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // Z = X + iY at k, conj(X) + i conj(Y) at -k
+#pragma unroll
+    for (int m = 0; m < MI; ++m) {
+      const int i = t + NT * m;
+      if (i < W * P) {
+        const int c = i / P, kz = i - c * P;
+        ex[c * CS + kz] = make_float2(X[m].x - Y[m].y, X[m].y + Y[m].x);
+        ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)] = make_float2(X[m].x + Y[m].y, Y[m].x - X[m].y);
+      }
+    }
+    __syncthreads();
+    {
+      float2 v[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = ex[c1 * CS + N2 * n1 + n2];
+      __syncthreads();
+      FS::template step1<1>(v, ex + c1 * CS, n2, tw);
+    }
+    __syncthreads();
+    if (has2 && !(c2 >= W && self_mirror)) {
+      // c2 and c1 differ in general: recompute column coordinates for c2
+      const int pk2 = ky0 + (c2 < W ? c2 : c2 - W);
+      if (pk2 < g.Py) {
+        const int ky2 = c2 < W ? pk2 : (g.Py - pk2) % g.Py;
+        const int kx2 = c2 < W ? kx : mkx;
+        float2 u[N2];
+        FS::template step2<1>(u, ex + c2 * CS, k1);
+        float2* dst = F2 + (long long)r * g.vz * plane_stride + (long long)kx2 * g.Py + ky2;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          const int vz = shift_slot(k1 + N1 * k2, g.nz, P);
+          if (vz >= 0) dst[(long long)vz * plane_stride] = u[k2];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int P>
+void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
+                 cudaStream_t st) {
+  constexpr int W = 8, N2 = Split<P>::N2;
+  const size_t smem = (size_t)2 * W * FourStep<P>::CS * sizeof(float2);
+  set_smem(k_zmac<P, W>, smem);
+  dim3 grid((unsigned)((g.Py + W - 1) / W), (unsigned)(g.Px / 2 + 1));
+  k_zmac<P, W><<<grid, 2 * W * N2, smem, st>>>(F1, UV, F2, tw, g, nrot);
+}
+
+// ---------------------------------------------------------------------------
+// prep_z (fixed volume, once): z-axis FFT of A's four packed fields, channel
+// separation via the mirror column, and the weights
+//   U_j = (w_a conj(A_a) - i w_b conj(A_b)) / 2,  V_j = (w_a conj(A_a) + i w_b conj(A_b)) / 2
+// for pairs j < 3 (channels a = 2j, b = 2j+1 with Eq. 6 weights), and
+// U_3 = conj(A_mask), stored for kx <= Px/2.
+// ---------------------------------------------------------------------------
+template <int P, int W>
+__global__ void __launch_bounds__(2 * W * Split<P>::N2)
+k_prep_z(const float2* __restrict__ F1, float2* __restrict__ UV, const float2* __restrict__ tw,
+         Geo g) {
+  using FS = FourStep<P>;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
+  constexpr int NC = 2 * W, NT = NC * N2, MI = (W * P + NT - 1) / NT;
+  extern __shared__ float2 ex[];
+  const int t = threadIdx.x;
+  const int kx = blockIdx.y, ky0 = blockIdx.x * W;
+  const int mkx = (g.Px - kx) % g.Px;
+  const long long hx = g.Px / 2 + 1;
+  const long long S7 = hx * g.Py * (long long)P;
+  const int c1 = t % NC, n2 = t / NC;
+  const int pk1 = ky0 + (c1 < W ? c1 : c1 - W);
+  const bool ok1 = pk1 < g.Py;
+  const int ky1 = c1 < W ? pk1 : (g.Py - pk1) % g.Py;
+  const int kx1 = c1 < W ? kx : mkx;
+  const bool has2 = t < NC * N1;
+  const int c2 = t % NC, k1 = t / NC;
+  const long long plane_stride = (long long)g.Px * g.Py;
+  const float wts[3][2] = {{1.f, 1.f}, {1.f, 2.f}, {2.f, 2.f}};
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    const float2* src = F1 + (long long)j * g.nz * plane_stride;
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const int z = N2 * n1 + n2;
+      v[n1] = (ok1 && z < g.nz) ? src[(long long)z * plane_stride + (long long)kx1 * g.Py + ky1]
+                                : make_float2(0.f, 0.f);
+    }
+    FS::template step1<-1>(v, ex + c1 * CS, n2, tw);
+    __syncthreads();
+    float2 u[N2];
+    if (has2) FS::template step2<-1>(u, ex + c2 * CS, k1);
+    __syncthreads();
+    if (has2) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) ex[c2 * CS + k1 + N1 * k2] = u[k2];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < MI; ++m) {
+      const int i = t + NT * m;
+      if (i < W * P) {
+        const int c = i / P, kz = i - c * P;
+        const int ky = ky0 + c;
+        if (ky < g.Py) {
+          const float2 h = ex[c * CS + kz];
+          const long long o = ((long long)kx * g.Py + ky) * P + kz;
+          if (j < 3) {
+            const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
+            // A_a = (h + hm)/2, A_b = -i (h - hm)/2
+            const float2 Aa = cscale(cadd(h, hm), 0.5f);
+            const float2 d = cscale(csub(h, hm), 0.5f);
+            const float2 Ab = make_float2(d.y, -d.x);
+            const float2 ca = cscale(cconj(Aa), wts[j][0]);
+            const float2 cb = cscale(cconj(Ab), wts[j][1]);
+            const float2 icb = make_float2(-cb.y, cb.x);          // i * cb
+            UV[(2 * j) * S7 + o] = cscale(csub(ca, icb), 0.5f);
+            UV[(2 * j + 1) * S7 + o] = cscale(cadd(ca, icb), 0.5f);
+          } else {
+            UV[6 * S7 + o] = cconj(h);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int P>
+void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g, cudaStream_t st) {
+  constexpr int W = 8, N2 = Split<P>::N2;
+  const size_t smem = (size_t)2 * W * FourStep<P>::CS * sizeof(float2);
+  set_smem(k_prep_z<P, W>, smem);
+  dim3 grid((unsigned)((g.Py + W - 1) / W), (unsigned)(g.Px / 2 + 1));
+  k_prep_z<P, W><<<grid, 2 * W * N2, smem, st>>>(F1, UV, tw, g);
+}
+
+// ---------------------------------------------------------------------------
+// inv_y: y-axis inverse FFT of every (vz, kx) row of F2, keeping 2ny-1 shift
+// rows, transposed so kx is contiguous.  Block: W consecutive kx rows.
+// ---------------------------------------------------------------------------
+template <int P, int W>
+__global__ void __launch_bounds__(W * Split<P>::N2)
+k_inv_y(const float2* __restrict__ F2, float2* __restrict__ F3, const float2* __restrict__ tw,
+        Geo g) {
+  using FS = FourStep<P>;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
+  extern __shared__ float2 ex[];
+  const int t = threadIdx.x;
+  const long long plane = blockIdx.x;               // r * vz + vz_i
+  const int kx0 = blockIdx.y * W;
+  {
+    const int row = t / N2, n2 = t - row * N2;
+    const int kx = kx0 + row;
+    float2 v[N1];
+    const float2* src = F2 + (plane * g.Px + kx) * (long long)P;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1)
+      v[n1] = (kx < g.Px) ? src[N2 * n1 + n2] : make_float2(0.f, 0.f);
+    FS::template step1<1>(v, ex + row * CS, n2, tw);
+  }
+  __syncthreads();
+  if (t < W * N1) {
+    const int col = t % W, k1 = t / W;
+    const int kx = kx0 + col;
+    if (kx < g.Px) {
+      float2 u[N2];
+      FS::template step2<1>(u, ex + col * CS, k1);
+      float2* dst = F3 + plane * (long long)g.vy * g.Px + kx;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int vy = shift_slot(k1 + N1 * k2, g.ny, P);
+        if (vy >= 0) dst[(long long)vy * g.Px] = u[k2];
+      }
+    }
+  }
+}
+
+template <int P>
+void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nrot, cudaStream_t st) {
+  constexpr int W = 16, N2 = Split<P>::N2;
+  const size_t smem = (size_t)W * FourStep<P>::CS * sizeof(float2);
+  set_smem(k_inv_y<P, W>, smem);
+  dim3 grid((unsigned)(nrot * g.vz), (unsigned)((g.Px + W - 1) / W));
+  k_inv_y<P, W><<<grid, W * N2, smem, st>>>(F2, F3, tw, g);
+}
+
+// ---------------------------------------------------------------------------
+// inv_x: x-axis inverse FFT of every (vz, vy) row of F3; at each valid shift
+// s = X / N (Eq. 5) where N >= the minimum overlap, and the block's argmax is
+// folded into the rotation's key with one atomicMax.  Optionally writes the
+// score map (-inf where invalid).  Block: ROWS consecutive vy of one plane.
+// ---------------------------------------------------------------------------
+template <int P, int ROWS>
+__global__ void __launch_bounds__((ROWS * Split<P>::N2 + 31) / 32 * 32)
+k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
+        unsigned long long* __restrict__ keys, float* __restrict__ map,
+        const float2* __restrict__ tw, Geo g) {
+  using FS = FourStep<P>;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, NT = (ROWS * N2 + 31) / 32 * 32;
+  extern __shared__ float2 ex[];
+  __shared__ unsigned long long red[NT / 32];
+  const int t = threadIdx.x;
+  const int plane = blockIdx.y;                       // r * vz + vz_i
+  const int r = plane / g.vz, vzi = plane - r * g.vz;
+  const int vy0 = blockIdx.x * ROWS;
+  if (t < ROWS * N2) {
+    const int lrow = t / N2, n2 = t - lrow * N2;
+    const int vyi = vy0 + lrow;
+    const float2* src = F3 + ((long long)plane * g.vy + vyi) * P;
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1)
+      v[n1] = (vyi < g.vy) ? src[N2 * n1 + n2] : make_float2(0.f, 0.f);
+    FS::template step1<1>(v, ex + lrow * CS, n2, tw);
+  }
+  __syncthreads();
+  unsigned long long best = 0ull;
+  if (t < ROWS * N1) {
+    const int lr = t / N1, k1 = t - lr * N1;
+    const int vyi = vy0 + lr;
+    if (vyi < g.vy) {
+      float2 u[N2];
+      FS::template step2<1>(u, ex + lr * CS, k1);
+      const float th = thr[r];
+      const unsigned row_lin = ((unsigned)vzi * (unsigned)g.vy + (unsigned)vyi) * (unsigned)g.vx;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int vxi = shift_slot(k1 + N1 * k2, g.nx, P);
+        if (vxi >= 0) {
+          const float2 zz = u[k2];
+          float s = __int_as_float(0xff800000);
+          if (zz.y >= th) {
+            s = __fdiv_rn(zz.x, zz.y);
+            const unsigned long long key = make_key(s, row_lin + (unsigned)vxi);
+            best = key > best ? key : best;
+          }
+          if (map) map[(long long)row_lin + vxi] = s;
+        }
+      }
+    }
+  }
+  // block max
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o > best ? o : best;
+  }
+  if ((t & 31) == 0) red[t >> 5] = best;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long b = 0ull;
+    for (int w = 0; w < NT / 32; ++w) b = red[w] > b ? red[w] : b;
+    if (b) atomicMax(&keys[r], b);
+  }
+}
+
+template <int P>
+void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys, float* map,
+                  const float2* tw, Geo g, int nrot, cudaStream_t st) {
+  constexpr int N2 = Split<P>::N2;
+  constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
+  const size_t smem = (size_t)ROWS * FourStep<P>::CS * sizeof(float2);
+  set_smem(k_inv_x<P, ROWS>, smem);
+  dim3 grid((unsigned)((g.vy + ROWS - 1) / ROWS), (unsigned)(nrot * g.vz));
+  k_inv_x<P, ROWS><<<grid, (ROWS * N2 + 31) / 32 * 32, smem, st>>>(F3, thr, keys, map, tw, g);
+}
+
+#define CSNGF_INSTANTIATE_PASSES(P)                                                              \
+  template void launch_fwd_x<P>(const float*, const uint8_t*, float2*, const float2*, Geo, int,  \
+                                cudaStream_t);                                                   \
+  template void launch_fwd_y<P>(const float2*, float2*, const float2*, Geo, int, cudaStream_t);  \
+  template void launch_zmac<P>(const float2*, const float2*, float2*, const float2*, Geo, int,   \
+                               cudaStream_t);                                                    \
+  template void launch_prep_z<P>(const float2*, float2*, const float2*, Geo, cudaStream_t);      \
+  template void launch_inv_y<P>(const float2*, float2*, const float2*, Geo, int, cudaStream_t);  \
+  template void launch_inv_x<P>(const float2*, const float*, unsigned long long*, float*,        \
+                                const float2*, Geo, int, cudaStream_t);
+
+}  // namespace csngf
