@@ -273,8 +273,8 @@ cs_ngf_status score_batch(cs_ngf_fixed* f, const float* B, const uint8_t* MB, in
   CS_CUDA(cudaMemsetAsync(f->keys, 0, sizeof(unsigned long long) * nb, st));
   {
     Stage sp(f, 0, st);
-    k_resample<<<dim3((unsigned)(g.nz * g.ny), (unsigned)nb), 128, 0, st>>>(
-        B, MB, f->rot_d + r0, g, f->Bh, f->Mh, f->msum);
+    k_resample<<<dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)(g.nz * nb)),
+                 dim3(32, 4), 0, st>>>(B, MB, f->rot_d + r0, g, f->Bh, f->Mh, f->msum);
   }
   if (cs_ngf_status s = check_launch("resample")) return s;
   const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
@@ -541,7 +541,8 @@ cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* ma
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
   const Geo& g = f->g;
-  k_resample<<<dim3((unsigned)(g.nz * g.ny), 1u), 128, 0, st>>>(B, maskB, f->rot_d, g, Bhat, Mhat, f->msum);
+  k_resample<<<dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz),
+               dim3(32, 4), 0, st>>>(B, maskB, f->rot_d, g, Bhat, Mhat, f->msum);
   return check_launch("resample");
 }
 

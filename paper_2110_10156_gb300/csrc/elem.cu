@@ -25,23 +25,31 @@ __device__ __forceinline__ AxisSample axis_sample(float p, int n) {
   return a;
 }
 
+// (1 - t) a + t b as two fused multiply-adds: a at t = 0, b at t = 1 exactly
+__device__ __forceinline__ float lerp_exact(float a, float b, float t) {
+  return fmaf(t, b, fmaf(-t, a, a));
+}
+
 __device__ __forceinline__ float lerp_rn(float a, float b, float t) {
   return __fadd_rn(a, __fmul_rn(t, __fsub_rn(b, a)));
 }
 }  // namespace
 
-__global__ void k_resample(const float* __restrict__ B, const uint8_t* __restrict__ MB,
-                           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
-                           uint8_t* __restrict__ Mh, int* __restrict__ msum) {
-  const int r = blockIdx.y;
-  const int row = blockIdx.x;                 // z * ny + y
-  const int z = row / g.ny, y = row - z * g.ny;
-  const RotMat R = rot[r];
-  const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1), cz = 0.5f * (float)(g.nz - 1);
-  const float dy = __fsub_rn((float)y, cy), dz = __fsub_rn((float)z, cz);
+__global__ void __launch_bounds__(128)
+k_resample(const float* __restrict__ B, const uint8_t* __restrict__ MB,
+           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
+           uint8_t* __restrict__ Mh, int* __restrict__ msum) {
+  // block: 32 x-consecutive voxels of 4 rows; grid (x tiles, y tiles, z * rotations)
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 4 + threadIdx.y;
+  const int r = blockIdx.z / g.nz, z = blockIdx.z - r * g.nz;
   int count = 0;
-  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
-    const float dx = __fsub_rn((float)x, cx);
+  if (x < g.nx && y < g.ny) {
+    const RotMat& R = rot[r];
+    const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1),
+                cz = 0.5f * (float)(g.nz - 1);
+    const float dx = __fsub_rn((float)x, cx), dy = __fsub_rn((float)y, cy),
+                dz = __fsub_rn((float)z, cz);
     float p[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -63,11 +71,12 @@ __global__ void k_resample(const float* __restrict__ B, const uint8_t* __restric
         v[k] = __ldg(&B[b000 + o[k]]);
         mk[k] = (float)__ldg(&MB[b000 + o[k]]);
       }
-      // intensity: lerps along x, y, z (contraction allowed)
-      float v00 = v[0] + ax.t * (v[1] - v[0]), v01 = v[2] + ax.t * (v[3] - v[2]);
-      float v10 = v[4] + ax.t * (v[5] - v[4]), v11 = v[6] + ax.t * (v[7] - v[6]);
-      float v0 = v00 + ay.t * (v01 - v00), v1 = v10 + ay.t * (v11 - v10);
-      val = v0 + az.t * (v1 - v0);
+      // intensity: lerps along x, y, z, exact at t = 0 and t = 1 so that
+      // quarter turns reproduce the voxels bit for bit
+      float v00 = lerp_exact(v[0], v[1], ax.t), v01 = lerp_exact(v[2], v[3], ax.t);
+      float v10 = lerp_exact(v[4], v[5], ax.t), v11 = lerp_exact(v[6], v[7], ax.t);
+      float v0 = lerp_exact(v00, v01, ay.t), v1 = lerp_exact(v10, v11, ay.t);
+      val = lerp_exact(v0, v1, az.t);
       // mask decision: same lerp order, round-to-nearest, no contraction
       float m00 = lerp_rn(mk[0], mk[1], ax.t), m01 = lerp_rn(mk[2], mk[3], ax.t);
       float m10 = lerp_rn(mk[4], mk[5], ax.t), m11 = lerp_rn(mk[6], mk[7], ax.t);
@@ -75,21 +84,21 @@ __global__ void k_resample(const float* __restrict__ B, const uint8_t* __restric
       float mm = lerp_rn(m0, m1, az.t);
       m = (mm >= 0.5f) ? 1 : 0;
     }
-    const long long idx = (long long)r * g.nvox + (long long)row * g.nx + x;
+    const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
     Bh[idx] = val;
     Mh[idx] = m;
-    count += m;
+    count = m;
   }
   // block reduction of the mask count
   for (int off = 16; off > 0; off >>= 1) count += __shfl_down_sync(0xffffffffu, count, off);
-  __shared__ int warp_sums[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ int warp_sums[4];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
   if (lane == 0) warp_sums[wid] = count;
   __syncthreads();
-  if (wid == 0) {
-    int c = (lane < (int)((blockDim.x + 31) >> 5)) ? warp_sums[lane] : 0;
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
-    if (lane == 0 && c) atomicAdd(&msum[r], c);
+  if (tid == 0) {
+    const int c = warp_sums[0] + warp_sums[1] + warp_sums[2] + warp_sums[3];
+    if (c) atomicAdd(&msum[r], c);
   }
 }
 

@@ -218,6 +218,32 @@ struct FourStep {
     }
   }
 
+  // Same as step1 when the input is zero for n1 >= N1/2 (a forward transform
+  // of data zero-padded from length <= N/2): the N1-point DFT splits into two
+  // N1/2-point DFTs, X[2m] = DFT(x)[m], X[2m+1] = DFT(x * W_N1^n)[m].
+  static constexpr int H = N1 / 2;
+  template <int S>
+  __device__ __forceinline__ static void step1_half(float2 (&v)[H], float2* ex_seq, int n2,
+                                                    const float2* __restrict__ twN) {
+    static_assert(N1 % 2 == 0, "half-zero step needs an even N1");
+    float2 e[H], o[H];
+    sfor<H>([&](auto nc) {
+      constexpr int n = decltype(nc)::value;
+      e[n] = v[n];
+      o[n] = tw_mul<N1, S, n>(v[n]);
+    });
+    Dft<H, S>::run(e);
+    Dft<H, S>::run(o);
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      const int ke = 2 * m, ko = 2 * m + 1;
+      float2 we = __ldg(&twN[n2 * ke]), wo = __ldg(&twN[n2 * ko]);
+      if (S > 0) { we.y = -we.y; wo.y = -wo.y; }
+      ex_seq[n2 * RS + ke] = (m == 0) ? e[m] : cmul(e[m], we);
+      ex_seq[n2 * RS + ko] = cmul(o[m], wo);
+    }
+  }
+
   // u[k2] = X[k1 + N1*k2]
   template <int S>
   __device__ __forceinline__ static void step2(float2 (&u)[N2], const float2* ex_seq, int k1) {

@@ -25,11 +25,11 @@ static void set_smem(K kern, size_t bytes) {
 // Block: ROWS rows of one slab; thread (row, n2) gathers x = N2*n1 + n2.
 // ---------------------------------------------------------------------------
 template <int P, int ROWS>
-__global__ void __launch_bounds__(ROWS * Split<P>::N2)
+__global__ void __launch_bounds__(ROWS * Split<P>::N2, 2)
 k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __restrict__ F0,
         const float2* __restrict__ tw, Geo g, long long nrows) {
   using FS = FourStep<P>;
-  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
   extern __shared__ float2 ex[];
   const int t = threadIdx.x;
   const int lrow = t / N2, n2 = t - lrow * N2;
@@ -39,7 +39,8 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
   const int y = row_ok ? (int)(grow - rz * g.ny) : 0;
   const int r = (int)(rz / g.nz), z = (int)(rz - (long long)r * g.nz);
 
-  float vx[N1], vy[N1], vz[N1], mm[N1];
+  // x = N2*n1 + n2 < nx <= P/2 only for n1 < N1/2: the upper half is zero
+  float vx[H], vy[H], vz[H], mm[H];
   const float* V = Bh + (long long)r * g.nvox;
   const uint8_t* M = Mh + (long long)r * g.nvox;
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
@@ -47,7 +48,7 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
   const int zm = max(z - 1, 0), zp = min(z + 1, g.nz - 1);
   const long long base = (long long)z * sz + (long long)y * sy;
 #pragma unroll
-  for (int n1 = 0; n1 < N1; ++n1) {
+  for (int n1 = 0; n1 < H; ++n1) {
     const int x = N2 * n1 + n2;
     vx[n1] = vy[n1] = vz[n1] = mm[n1] = 0.0f;
     if (row_ok && x < g.nx) {
@@ -67,9 +68,9 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
   const long long rows_per_field = (long long)g.nz * g.ny;
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
-    float2 v[N1];
+    float2 v[H];
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
+    for (int n1 = 0; n1 < H; ++n1) {
       const float m = mm[n1];
       switch (j) {
         case 0: v[n1] = make_float2(m * vx[n1] * vx[n1], m * vy[n1] * vy[n1]); break;
@@ -78,7 +79,7 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
         default: v[n1] = make_float2(m, 0.0f); break;
       }
     }
-    FS::template step1<-1>(v, ex + lrow * CS, n2, tw);
+    FS::template step1_half<-1>(v, ex + lrow * CS, n2, tw);
     __syncthreads();
     if (t < ROWS * N1) {
       const int lr = t / N1, k1 = t - lr * N1;
@@ -129,13 +130,13 @@ k_fwd_y(const float2* __restrict__ F0, float2* __restrict__ F1, const float2* __
     const int col = t % W, n2 = t / W;
     const int kx = kx0 + col;
     const float2* src = F0 + plane * (long long)g.ny * g.Px;
-    float2 v[N1];
+    float2 v[FS::H];                      // y < ny <= P/2: upper half is zero
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
+    for (int n1 = 0; n1 < FS::H; ++n1) {
       const int y = N2 * n1 + n2;
       v[n1] = (y < g.ny && kx < g.Px) ? src[(long long)y * g.Px + kx] : make_float2(0.f, 0.f);
     }
-    FS::template step1<-1>(v, ex + col * CS, n2, tw);
+    FS::template step1_half<-1>(v, ex + col * CS, n2, tw);
   }
   __syncthreads();
   if (t < W * N1) {
@@ -170,19 +171,23 @@ void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nro
 // fixed spectra tile stays in L2.
 // ---------------------------------------------------------------------------
 template <int P, int W>
-__global__ void __launch_bounds__(2 * W * Split<P>::N2)
+__global__ void __launch_bounds__(2 * W * Split<P>::N2, 2)
 k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot) {
   using FS = FourStep<P>;
-  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
   constexpr int NC = 2 * W, NT = NC * N2, MI = (W * P + NT - 1) / NT;
-  extern __shared__ float2 ex[];
+  extern __shared__ float2 smem[];
+  float2* ex = smem;                       // [NC][CS] transform exchange
+  float2* xacc = smem + NC * CS;           // [W*P] numerator spectrum X
+  float2* yacc = xacc + W * P;             // [W*P] overlap spectrum Y
   const int t = threadIdx.x;
   const int kx = blockIdx.y, ky0 = blockIdx.x * W;
   const int mkx = (g.Px - kx) % g.Px;
   const bool self_mirror = (2 * kx) % g.Px == 0;
   const long long hx = g.Px / 2 + 1;
   const long long S7 = hx * g.Py * (long long)P;
+  const long long plane_stride = (long long)g.Px * g.Py;
 
   // step-1 role: column c1 (fastest), n2
   const int c1 = t % NC, n2 = t / NC;
@@ -190,26 +195,32 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
   const bool ok1 = pk1 < g.Py;
   const int ky1 = c1 < W ? pk1 : (g.Py - pk1) % g.Py;
   const int kx1 = c1 < W ? kx : mkx;
+  const long long col_off = (long long)kx1 * g.Py + ky1;
   // step-2 role: column c2 (fastest), k1
   const bool has2 = t < NC * N1;
   const int c2 = t % NC, k1 = t / NC;
-  const long long plane_stride = (long long)g.Px * g.Py;
+
+  // z = N2*n1 + n2 < nz <= P/2 only for n1 < N1/2
+  float2 pf[H];
+  auto fetch = [&](int r, int j) {
+    const float2* src = F1 + ((long long)r * 4 + j) * g.nz * plane_stride + col_off;
+#pragma unroll
+    for (int n1 = 0; n1 < H; ++n1) {
+      const int z = N2 * n1 + n2;
+      pf[n1] = (ok1 && z < g.nz) ? src[(long long)z * plane_stride] : make_float2(0.f, 0.f);
+    }
+  };
+  if (nrot > 0) fetch(0, 0);
 
   for (int r = 0; r < nrot; ++r) {
-    float2 X[MI], Y[MI];
-#pragma unroll
-    for (int m = 0; m < MI; ++m) X[m] = Y[m] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
-      const float2* src = F1 + ((long long)r * 4 + j) * g.nz * plane_stride;
-      float2 v[N1];
+      float2 v[H];
 #pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) {
-        const int z = N2 * n1 + n2;
-        v[n1] = (ok1 && z < g.nz) ? src[(long long)z * plane_stride + (long long)kx1 * g.Py + ky1]
-                                  : make_float2(0.f, 0.f);
-      }
-      FS::template step1<-1>(v, ex + c1 * CS, n2, tw);
+      for (int n1 = 0; n1 < H; ++n1) v[n1] = pf[n1];
+      if (j < 3) fetch(r, j + 1);              // next field's loads overlap this one's work
+      else if (r + 1 < nrot) fetch(r + 1, 0);
+      FS::template step1_half<-1>(v, ex + c1 * CS, n2, tw);
       __syncthreads();
       float2 u[N2];
       if (has2) FS::template step2<-1>(u, ex + c2 * CS, k1);
@@ -219,24 +230,24 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
         for (int k2 = 0; k2 < N2; ++k2) ex[c2 * CS + k1 + N1 * k2] = u[k2];
       }
       __syncthreads();
+      // Eq. 7-8: accumulate the weighted channel products (separated through
+      // the mirror column) and the mask product
 #pragma unroll
       for (int m = 0; m < MI; ++m) {
         const int i = t + NT * m;
         if (i < W * P) {
           const int c = i / P, kz = i - c * P;
-          const int ky = ky0 + c;
-          if (ky < g.Py) {
-            const float2 h = ex[c * CS + kz];
-            const long long o = ((long long)kx * g.Py + ky) * P + kz;
-            if (j < 3) {
-              const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
-              const float2 U = __ldg(&UV[(2 * j) * S7 + o]);
-              const float2 V = __ldg(&UV[(2 * j + 1) * S7 + o]);
-              X[m] = cadd(X[m], cadd(cmul(U, h), cmul(V, hm)));
-            } else {
-              const float2 U = __ldg(&UV[6 * S7 + o]);
-              Y[m] = cadd(Y[m], cmul(U, h));
-            }
+          const int ky = min(ky0 + c, g.Py - 1);
+          const float2 h = ex[c * CS + kz];
+          const long long o = ((long long)kx * g.Py + ky) * P + kz;
+          if (j < 3) {
+            const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
+            const float2 U = __ldg(&UV[(2 * j) * S7 + o]);
+            const float2 V = __ldg(&UV[(2 * j + 1) * S7 + o]);
+            const float2 add = cadd(cmul(U, h), cmul(V, hm));
+            xacc[i] = (j == 0) ? add : cadd(xacc[i], add);
+          } else {
+            yacc[i] = cmul(__ldg(&UV[6 * S7 + o]), h);
           }
         }
       }
@@ -248,8 +259,9 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
       const int i = t + NT * m;
       if (i < W * P) {
         const int c = i / P, kz = i - c * P;
-        ex[c * CS + kz] = make_float2(X[m].x - Y[m].y, X[m].y + Y[m].x);
-        ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)] = make_float2(X[m].x + Y[m].y, Y[m].x - X[m].y);
+        const float2 X = xacc[i], Y = yacc[i];
+        ex[c * CS + kz] = make_float2(X.x - Y.y, X.y + Y.x);
+        ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)] = make_float2(X.x + Y.y, Y.x - X.y);
       }
     }
     __syncthreads();
@@ -262,7 +274,6 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
     }
     __syncthreads();
     if (has2 && !(c2 >= W && self_mirror)) {
-      // c2 and c1 differ in general: recompute column coordinates for c2
       const int pk2 = ky0 + (c2 < W ? c2 : c2 - W);
       if (pk2 < g.Py) {
         const int ky2 = c2 < W ? pk2 : (g.Py - pk2) % g.Py;
@@ -285,7 +296,7 @@ template <int P>
 void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
                  cudaStream_t st) {
   constexpr int W = 8, N2 = Split<P>::N2;
-  const size_t smem = (size_t)2 * W * FourStep<P>::CS * sizeof(float2);
+  const size_t smem = ((size_t)2 * W * FourStep<P>::CS + (size_t)2 * W * P) * sizeof(float2);
   set_smem(k_zmac<P, W>, smem);
   dim3 grid((unsigned)((g.Py + W - 1) / W), (unsigned)(g.Px / 2 + 1));
   k_zmac<P, W><<<grid, 2 * W * N2, smem, st>>>(F1, UV, F2, tw, g, nrot);
@@ -323,14 +334,14 @@ k_prep_z(const float2* __restrict__ F1, float2* __restrict__ UV, const float2* _
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
     const float2* src = F1 + (long long)j * g.nz * plane_stride;
-    float2 v[N1];
+    float2 v[FS::H];                      // z < nz <= P/2: upper half is zero
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
+    for (int n1 = 0; n1 < FS::H; ++n1) {
       const int z = N2 * n1 + n2;
       v[n1] = (ok1 && z < g.nz) ? src[(long long)z * plane_stride + (long long)kx1 * g.Py + ky1]
                                 : make_float2(0.f, 0.f);
     }
-    FS::template step1<-1>(v, ex + c1 * CS, n2, tw);
+    FS::template step1_half<-1>(v, ex + c1 * CS, n2, tw);
     __syncthreads();
     float2 u[N2];
     if (has2) FS::template step2<-1>(u, ex + c2 * CS, k1);

@@ -1,0 +1,59 @@
+"""Full-size parity: the 150^3 / 320^3 workload with 1000 rotations, scored in
+the same launch configuration the bench times (automatic batch), checked
+against the FP64 oracle on sampled rotations and by properties on all."""
+import numpy as np
+import pytest
+
+from oracle import cs_ngf_oracle as O
+from paper_2110_10156_gb300 import synth
+from tests.parity_util import check_best_against_map
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_10156_gb300 import build
+    build.build()
+    from paper_2110_10156_gb300 import cs_ngf
+    return cs_ngf
+
+
+@pytest.fixture(scope="module")
+def pair150():
+    return synth.config_pair(1)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_150_cubed_1000_rotations(cs, pair150):
+    p = pair150
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA))
+    assert f.pad == (320, 320, 320)
+    assert f.sum_mask_a == int(p.MA.sum())
+    sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+    R = len(p.quats)
+    assert sc.shape == (R,) and sh.shape == (R, 3)
+    # properties at any size: scores are averages of values in [0, 1]; shifts in range
+    fin = np.isfinite(sc)
+    assert fin.all()
+    assert sc.min() >= -1e-6 and sc.max() <= 1 + 1e-6
+    assert np.all(np.abs(sh) <= 149)
+    # the generator's truth is recovered at q_true and overall
+    assert tuple(sh[p.true_index]) == p.t_zyx
+    assert int(np.argmax(sc)) == p.true_index
+    score, ri, chi = f.align(dev(p.B), dev(p.MB), p.quats)
+    assert ri == p.true_index and chi == p.t_zyx
+    # sampled rotations against the oracle's full map (FFT form at 320^3)
+    rng = np.random.default_rng(99)
+    sample = [p.true_index] + [int(i) for i in rng.choice(R, 2, replace=False)]
+    for r in sample:
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, p.quats[r], pad=(320, 320, 320))
+        check_best_against_map(omap, sc[r], sh[r])
+    f.release()
