@@ -162,6 +162,44 @@ cs_ngf_status cs_ngf_stage_times(cs_ngf_fixed* f, double* ms, int64_t* launches)
 /* Number of kernel launches this library has made in the process. */
 int64_t cs_ngf_launch_count(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free scoring for small volumes.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc.  Examples
+ * are code running inside another framework's memory pool or allocator hooks,
+ * real-time loops where an allocation may block or fail at the worst moment,
+ * and processes held to a fixed device-memory budget.
+ *
+ * It computes what cs_ngf_prepare_fixed + cs_ngf_score_rotations compute for
+ * the same inputs, using the same kernels, one rotation at a time.  It
+ * allocates nothing: no cudaMalloc, no cudaFree and no allocating library
+ * routine.  All scratch memory is a single file-scope device array of
+ * CS_NGF_NOALLOC_SCRATCH_BYTES bytes (about 13.4 MiB).  Every GPU that loads
+ * this library holds that array until the process exits.
+ *   A, maskA, B, maskB  device, [nz][ny][nx] float32 / uint8
+ *   dims                host {nz, ny, nx}, each in [2, CS_NGF_NOALLOC_MAX_DIM];
+ *                       larger sizes are rejected with EINVAL and a message
+ *   eps, gamma          as in cs_ngf_config
+ *   quats               host float64 [R][4] (w, x, y, z), read during the call
+ *   best_score          device float32 [R]
+ *   best_shift          device int32 [R][3]
+ * Work is enqueued on `stream` and the call returns without waiting for it.
+ * The first call on a device does a set-up step with that device current: it
+ * looks up the device address of the scratch array.  Make that first call
+ * before any stream capture.
+ * Every call uses the same scratch array, which keeps the previous call's
+ * contents.  What must start at zero is cleared on the stream at the start of
+ * each call.  Calls whose GPU work overlaps (several host threads, or several
+ * streams without ordering between them) race on the scratch array and give
+ * wrong results: serialise them.
+ * Errors: EINVAL, ECUDA (detail in cs_ngf_last_error()). */
+#define CS_NGF_NOALLOC_MAX_DIM 32
+#define CS_NGF_NOALLOC_SCRATCH_BYTES 14026496
+cs_ngf_status cs_ngf_score_rotations_noalloc(const float* A, const uint8_t* maskA, const float* B,
+                                             const uint8_t* maskB, const int32_t dims[3],
+                                             float eps, float gamma, const double* quats,
+                                             int32_t R, float* best_score, int32_t* best_shift,
+                                             void* stream);
+
 /* Sizes and FFT lengths of a handle.  info: host. */
 cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info);
 

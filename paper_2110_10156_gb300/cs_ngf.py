@@ -28,7 +28,7 @@ EXPORTED = (
     "cs_ngf_score_rotations_host", "cs_ngf_align", "cs_ngf_score_map", "cs_ngf_resample",
     "cs_ngf_get_info", "cs_ngf_release", "cs_ngf_status_string", "cs_ngf_last_error",
     "cs_ngf_auto_pad", "cs_ngf_update_fixed", "cs_ngf_set_profiling", "cs_ngf_stage_times",
-    "cs_ngf_launch_count",
+    "cs_ngf_launch_count", "cs_ngf_score_rotations_noalloc",
 )
 
 STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "other")
@@ -66,6 +66,9 @@ _lib.cs_ngf_auto_pad.restype = _i32
 _lib.cs_ngf_update_fixed.argtypes = [_vp, _vp, _vp, _vp]
 _lib.cs_ngf_set_profiling.argtypes = [_vp, _i32]
 _lib.cs_ngf_stage_times.argtypes = [_vp, _p(ctypes.c_double), _p(ctypes.c_int64)]
+_lib.cs_ngf_score_rotations_noalloc.argtypes = [_vp, _vp, _vp, _vp, _p(_i32), ctypes.c_float,
+                                                 ctypes.c_float, _vp, _i32, _vp, _vp, _vp]
+_lib.cs_ngf_score_rotations_noalloc.restype = _i32
 _lib.cs_ngf_launch_count.argtypes = []
 _lib.cs_ngf_launch_count.restype = ctypes.c_int64
 for _name in ("cs_ngf_update_fixed", "cs_ngf_set_profiling", "cs_ngf_stage_times",
@@ -274,6 +277,32 @@ class Fixed:
             self.release()
         except Exception:
             pass
+
+
+def score_rotations_noalloc(A, MA, B, MB, quats, eps=1e-5, gamma=0.5, out_score=None,
+                            out_shift=None, stream=None):
+    """Allocation-free scoring for volumes up to 32 per axis
+    (cs_ngf_score_rotations_noalloc): the library allocates no device memory;
+    its scratch is a fixed static device array shared by all calls, so calls
+    must not overlap on the GPU.  The outputs are allocated here by torch
+    unless given."""
+    import torch
+    dims = tuple(int(d) for d in A.shape)
+    q = _quats(quats)
+    R = q.shape[0]
+    if out_score is None:
+        out_score = torch.empty(R, dtype=torch.float32, device=A.device)
+    if out_shift is None:
+        out_shift = torch.empty((R, 3), dtype=torch.int32, device=A.device)
+    d = (ctypes.c_int32 * 3)(*dims)
+    _check(_lib.cs_ngf_score_rotations_noalloc(
+        _dev_ptr(A, torch.float32, "A"), _dev_ptr(MA, torch.uint8, "maskA"),
+        _dev_ptr(B, torch.float32, "B"), _dev_ptr(MB, torch.uint8, "maskB"), d,
+        float(eps), float(gamma), q.ctypes.data_as(ctypes.c_void_p), R,
+        _dev_ptr(out_score, torch.float32, "best_score"),
+        _dev_ptr(out_shift, torch.int32, "best_shift"), _stream_ptr(stream)),
+        "cs_ngf_score_rotations_noalloc")
+    return out_score, out_shift
 
 
 def prepare_fixed(A, MA, **kw) -> Fixed:

@@ -16,8 +16,15 @@
 using namespace csngf;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace csngf {
+// lets other translation units of the library report through cs_ngf_last_error
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace csngf
+
+namespace {
 
 cs_ngf_status fail(cs_ngf_status s, const std::string& msg) {
   g_last_error = msg;
