@@ -170,17 +170,28 @@ void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nro
 // keeping the 2nz-1 shift planes.  Loops over the batch's rotations so the
 // fixed spectra tile stays in L2.
 // ---------------------------------------------------------------------------
-template <int P, int W>
-__global__ void __launch_bounds__(2 * W * Split<P>::N2, 2)
+template <int P>
+struct ZmacCfg {
+  // primary columns per block: the block's tile of the seven fixed spectra
+  // (7 * W * P complex values) stays in shared memory for the whole batch
+  static constexpr int W = P <= 320 ? 8 : 4;
+  static constexpr int NT = 2 * W * Split<P>::N2;
+  static constexpr size_t smem_bytes =
+      ((size_t)7 * W * P + (size_t)2 * W * FourStep<P>::CS) * sizeof(float2);
+};
+
+template <int P>
+__global__ void __launch_bounds__(ZmacCfg<P>::NT, 1)
 k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot) {
   using FS = FourStep<P>;
+  constexpr int W = ZmacCfg<P>::W;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
-  constexpr int NC = 2 * W, NT = NC * N2, MI = (W * P + NT - 1) / NT;
+  constexpr int NC = 2 * W, NT = ZmacCfg<P>::NT, MI = (W * P + NT - 1) / NT;
+  constexpr int TILE = W * P;                 // complex values per fixed-spectra tile
   extern __shared__ float2 smem[];
-  float2* ex = smem;                       // [NC][CS] transform exchange
-  float2* xacc = smem + NC * CS;           // [W*P] numerator spectrum X
-  float2* yacc = xacc + W * P;             // [W*P] overlap spectrum Y
+  float2* uvs = smem;                         // [7][W][P] fixed-spectra weights
+  float2* ex = smem + 7 * TILE;               // [NC][CS] transform exchange
   const int t = threadIdx.x;
   const int kx = blockIdx.y, ky0 = blockIdx.x * W;
   const int mkx = (g.Px - kx) % g.Px;
@@ -212,7 +223,22 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
   };
   if (nrot > 0) fetch(0, 0);
 
+  // the block's fixed-spectra tile: 7 contiguous runs of W*P values (rows
+  // ky0..ky0+W-1 are contiguous in [kx][ky][kz]); rows past Py are zero
+  {
+    const int valid = min(W, g.Py - ky0) * P;
+    for (int a = 0; a < 7; ++a) {
+      const float4* src = reinterpret_cast<const float4*>(UV + a * S7 + ((long long)kx * g.Py + ky0) * P);
+      float4* dst = reinterpret_cast<float4*>(uvs + a * TILE);
+      for (int q = t; q < TILE / 2; q += NT)
+        dst[q] = (2 * q < valid) ? __ldg(&src[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+
   for (int r = 0; r < nrot; ++r) {
+    float2 X[MI], Y[MI];
+#pragma unroll
+    for (int m = 0; m < MI; ++m) X[m] = Y[m] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
       float2 v[H];
@@ -230,24 +256,29 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
         for (int k2 = 0; k2 < N2; ++k2) ex[c2 * CS + k1 + N1 * k2] = u[k2];
       }
       __syncthreads();
-      // Eq. 7-8: accumulate the weighted channel products (separated through
-      // the mirror column) and the mask product
+      // Eq. 7-8: the weighted channel products (separated through the mirror
+      // column) and the mask product, accumulated in registers
+      if (j < 3) {
+        const float2* Us = uvs + (2 * j) * TILE;
+        const float2* Vs = uvs + (2 * j + 1) * TILE;
 #pragma unroll
-      for (int m = 0; m < MI; ++m) {
-        const int i = t + NT * m;
-        if (i < W * P) {
-          const int c = i / P, kz = i - c * P;
-          const int ky = min(ky0 + c, g.Py - 1);
-          const float2 h = ex[c * CS + kz];
-          const long long o = ((long long)kx * g.Py + ky) * P + kz;
-          if (j < 3) {
+        for (int m = 0; m < MI; ++m) {
+          const int i = t + NT * m;
+          if (i < TILE) {
+            const int c = i / P, kz = i - c * P;
+            const float2 h = ex[c * CS + kz];
             const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
-            const float2 U = __ldg(&UV[(2 * j) * S7 + o]);
-            const float2 V = __ldg(&UV[(2 * j + 1) * S7 + o]);
-            const float2 add = cadd(cmul(U, h), cmul(V, hm));
-            xacc[i] = (j == 0) ? add : cadd(xacc[i], add);
-          } else {
-            yacc[i] = cmul(__ldg(&UV[6 * S7 + o]), h);
+            X[m] = cadd(X[m], cadd(cmul(Us[i], h), cmul(Vs[i], hm)));
+          }
+        }
+      } else {
+        const float2* Ms = uvs + 6 * TILE;
+#pragma unroll
+        for (int m = 0; m < MI; ++m) {
+          const int i = t + NT * m;
+          if (i < TILE) {
+            const int c = i / P, kz = i - c * P;
+            Y[m] = cmul(Ms[i], ex[c * CS + kz]);
           }
         }
       }
@@ -257,11 +288,10 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
 #pragma unroll
     for (int m = 0; m < MI; ++m) {
       const int i = t + NT * m;
-      if (i < W * P) {
+      if (i < TILE) {
         const int c = i / P, kz = i - c * P;
-        const float2 X = xacc[i], Y = yacc[i];
-        ex[c * CS + kz] = make_float2(X.x - Y.y, X.y + Y.x);
-        ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)] = make_float2(X.x + Y.y, Y.x - X.y);
+        ex[c * CS + kz] = make_float2(X[m].x - Y[m].y, X[m].y + Y[m].x);
+        ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)] = make_float2(X[m].x + Y[m].y, Y[m].x - X[m].y);
       }
     }
     __syncthreads();
@@ -295,11 +325,10 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
 template <int P>
 void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
                  cudaStream_t st) {
-  constexpr int W = 8, N2 = Split<P>::N2;
-  const size_t smem = ((size_t)2 * W * FourStep<P>::CS + (size_t)2 * W * P) * sizeof(float2);
-  set_smem(k_zmac<P, W>, smem);
-  dim3 grid((unsigned)((g.Py + W - 1) / W), (unsigned)(g.Px / 2 + 1));
-  k_zmac<P, W><<<grid, 2 * W * N2, smem, st>>>(F1, UV, F2, tw, g, nrot);
+  using C = ZmacCfg<P>;
+  set_smem(k_zmac<P>, C::smem_bytes);
+  dim3 grid((unsigned)((g.Py + C::W - 1) / C::W), (unsigned)(g.Px / 2 + 1));
+  k_zmac<P><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot);
 }
 
 // ---------------------------------------------------------------------------
