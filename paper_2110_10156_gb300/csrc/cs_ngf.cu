@@ -109,6 +109,7 @@ struct cs_ngf_fixed {
   float2* UV = nullptr;
   float* Bh = nullptr;
   uint8_t* Mh = nullptr;
+  float2* BM = nullptr;        // (B, mask) pairs of the current call
   float2* F02 = nullptr;
   float2* F13 = nullptr;
   int* msum = nullptr;
@@ -189,6 +190,7 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->UV);
   cudaFree(f->Bh);
   cudaFree(f->Mh);
+  cudaFree(f->BM);
   cudaFree(f->F02);
   cudaFree(f->F13);
   cudaFree(f->msum);
@@ -272,16 +274,22 @@ cs_ngf_status run_transforms(cs_ngf_fixed* f, int nb, float* map, cudaStream_t s
   return CS_NGF_OK;
 }
 
-// score rotations [r0, r0 + nb) whose matrices are at f->rot_d + r0
-cs_ngf_status score_batch(cs_ngf_fixed* f, const float* B, const uint8_t* MB, int r0, int nb,
+// (B, M_B) -> f->BM, shared by every rotation of the call
+cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st) {
+  { Stage sp(f, 0, st); k_pack_bm<<<512, 256, 0, st>>>(B, MB, f->g.nvox, f->BM); }
+  return check_launch("pack");
+}
+
+// score rotations [r0, r0 + nb) whose matrices are at f->rot_d + r0, with the
+// floating volume already packed in f->BM
+cs_ngf_status score_batch(cs_ngf_fixed* f, int r0, int nb,
                           float* best_score, int32_t* best_shift, float* map, cudaStream_t st) {
   const Geo& g = f->g;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int) * nb, st));
   CS_CUDA(cudaMemsetAsync(f->keys, 0, sizeof(unsigned long long) * nb, st));
   {
     Stage sp(f, 0, st);
-    k_resample<<<dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)(g.nz * nb)),
-                 dim3(32, 4), 0, st>>>(B, MB, f->rot_d + r0, g, f->Bh, f->Mh, f->msum);
+    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, f->rot_d + r0, g, f->Bh, f->Mh, f->msum);
   }
   if (cs_ngf_status s = check_launch("resample")) return s;
   const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
@@ -331,9 +339,10 @@ cs_ngf_status score_all(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cons
   if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
   if (!best_score || !best_shift) return fail(CS_NGF_EINVAL, "output pointer is NULL");
   if (cs_ngf_status s = upload_rotations(f, quats, R, st)) return s;
+  if (cs_ngf_status s = pack_floating(f, B, MB, st)) return s;
   for (int r0 = 0; r0 < R; r0 += f->batch) {
     const int nb = std::min(f->batch, R - r0);
-    if (cs_ngf_status s = score_batch(f, B, MB, r0, nb, best_score, best_shift, nullptr, st)) return s;
+    if (cs_ngf_status s = score_batch(f, r0, nb, best_score, best_shift, nullptr, st)) return s;
   }
   return CS_NGF_OK;
 }
@@ -421,6 +430,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   f->f02_elems = std::max(f0, f2);
   f->f13_elems = std::max(f1, f3);
   const size_t per_rot = (f->f02_elems + f->f13_elems) * sizeof(float2) + (size_t)g.nvox * 5;
+  const size_t shared_ws = (size_t)g.nvox * sizeof(float2);
   const size_t uv_elems = (size_t)7 * (g.Px / 2 + 1) * g.Py * g.Pz;
   int batch = cfg.batch;
   if (batch == 0) {
@@ -440,13 +450,14 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->UV, uv_elems));
   CS_TRYC(dalloc(&f->Bh, (size_t)batch * g.nvox));
   CS_TRYC(dalloc(&f->Mh, (size_t)batch * g.nvox));
+  CS_TRYC(dalloc(&f->BM, (size_t)g.nvox));
   CS_TRYC(dalloc(&f->F02, (size_t)batch * f->f02_elems));
   CS_TRYC(dalloc(&f->F13, (size_t)batch * f->f13_elems));
   CS_TRYC(dalloc(&f->msum, (size_t)batch));
   CS_TRYC(dalloc(&f->thr, (size_t)batch));
   CS_TRYC(dalloc(&f->keys, (size_t)batch));
   f->fixed_bytes = uv_elems * sizeof(float2);
-  f->workspace_bytes = (size_t)batch * per_rot;
+  f->workspace_bytes = (size_t)batch * per_rot + shared_ws;
   for (int a = 0; a < 3; ++a) {
     f->tw[a] = nullptr;
     for (int b = 0; b < a; ++b)
@@ -535,7 +546,8 @@ cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* m
   cudaStream_t st = (cudaStream_t)stream;
   if (cs_ngf_status s = ensure_results(f, 1)) return s;
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
-  return score_batch(f, B, maskB, 0, 1, f->res_score, f->res_shift, map, st);
+  if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
+  return score_batch(f, 0, 1, f->res_score, f->res_shift, map, st);
 }
 
 cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
@@ -548,8 +560,8 @@ cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* ma
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
   const Geo& g = f->g;
-  k_resample<<<dim3((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 3) / 4), (unsigned)g.nz),
-               dim3(32, 4), 0, st>>>(B, maskB, f->rot_d, g, Bhat, Mhat, f->msum);
+  if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
+  k_resample<<<resample_grid(g, 1), 128, 0, st>>>(f->BM, f->rot_d, g, Bhat, Mhat, f->msum);
   return check_launch("resample");
 }
 

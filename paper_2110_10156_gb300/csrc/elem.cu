@@ -35,55 +35,71 @@ __device__ __forceinline__ float lerp_rn(float a, float b, float t) {
 }
 }  // namespace
 
+// B and its mask packed as (value, 0/1) pairs, so each trilinear corner is
+// one 8-byte load (the volume is shared by every rotation of a call)
+__global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict__ MB, long long n,
+                          float2* __restrict__ BM) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    BM[i] = make_float2(B[i], MB[i] ? 1.0f : 0.0f);
+}
+
+__device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, const RotMat& R,
+                                               const Geo& g, int x, int y, int z, float& val,
+                                               uint8_t& m) {
+  const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1),
+              cz = 0.5f * (float)(g.nz - 1);
+  const float dx = __fsub_rn((float)x, cx), dy = __fsub_rn((float)y, cy),
+              dz = __fsub_rn((float)z, cz);
+  float p[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float acc = __fmul_rn(R.m[3 * i + 0], dx);
+    acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 1], dy));
+    acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 2], dz));
+    p[i] = __fadd_rn(acc, i == 0 ? cx : (i == 1 ? cy : cz));
+  }
+  AxisSample ax = axis_sample(p[0], g.nx), ay = axis_sample(p[1], g.ny), az = axis_sample(p[2], g.nz);
+  val = 0.0f;
+  m = 0;
+  if (ax.inside && ay.inside && az.inside) {
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    const long long b000 = (long long)az.i0 * sz + (long long)ay.i0 * sy + ax.i0;
+    const long long o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+    float2 c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c[k] = __ldg(&BM[b000 + o[k]]);
+    // intensity: lerps along x, y, z, exact at t = 0 and t = 1 so that
+    // quarter turns reproduce the voxels bit for bit
+    float v00 = lerp_exact(c[0].x, c[1].x, ax.t), v01 = lerp_exact(c[2].x, c[3].x, ax.t);
+    float v10 = lerp_exact(c[4].x, c[5].x, ax.t), v11 = lerp_exact(c[6].x, c[7].x, ax.t);
+    float v0 = lerp_exact(v00, v01, ay.t), v1 = lerp_exact(v10, v11, ay.t);
+    val = lerp_exact(v0, v1, az.t);
+    // mask decision: same lerp order, round-to-nearest, no contraction
+    float m00 = lerp_rn(c[0].y, c[1].y, ax.t), m01 = lerp_rn(c[2].y, c[3].y, ax.t);
+    float m10 = lerp_rn(c[4].y, c[5].y, ax.t), m11 = lerp_rn(c[6].y, c[7].y, ax.t);
+    float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
+    float mm = lerp_rn(m0, m1, az.t);
+    m = (mm >= 0.5f) ? 1 : 0;
+  }
+}
+
+// Section 3.2 resample.  Block: 8 x 4 x 4 voxels (x fastest), so one warp's
+// sample points form a compact rotated 8 x 4 patch.
+// Grid: (x tiles, y tiles, z tiles * rotations).
 __global__ void __launch_bounds__(128)
-k_resample(const float* __restrict__ B, const uint8_t* __restrict__ MB,
-           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
-           uint8_t* __restrict__ Mh, int* __restrict__ msum) {
-  // block: 32 x-consecutive voxels of 4 rows; grid (x tiles, y tiles, z * rotations)
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * 4 + threadIdx.y;
-  const int r = blockIdx.z / g.nz, z = blockIdx.z - r * g.nz;
+k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
+           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum) {
+  const int ztiles = (g.nz + 3) / 4;
+  const int r = blockIdx.z / ztiles, zt = blockIdx.z - r * ztiles;
+  const int x = blockIdx.x * 8 + (threadIdx.x & 7);
+  const int y = blockIdx.y * 4 + ((threadIdx.x >> 3) & 3);
+  const int z = zt * 4 + (threadIdx.x >> 5);
   int count = 0;
-  if (x < g.nx && y < g.ny) {
-    const RotMat& R = rot[r];
-    const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1),
-                cz = 0.5f * (float)(g.nz - 1);
-    const float dx = __fsub_rn((float)x, cx), dy = __fsub_rn((float)y, cy),
-                dz = __fsub_rn((float)z, cz);
-    float p[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      float acc = __fmul_rn(R.m[3 * i + 0], dx);
-      acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 1], dy));
-      acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 2], dz));
-      p[i] = __fadd_rn(acc, i == 0 ? cx : (i == 1 ? cy : cz));
-    }
-    AxisSample ax = axis_sample(p[0], g.nx), ay = axis_sample(p[1], g.ny), az = axis_sample(p[2], g.nz);
-    float val = 0.0f;
-    uint8_t m = 0;
-    if (ax.inside && ay.inside && az.inside) {
-      const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-      const long long b000 = (long long)az.i0 * sz + (long long)ay.i0 * sy + ax.i0;
-      const long long o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
-      float v[8], mk[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        v[k] = __ldg(&B[b000 + o[k]]);
-        mk[k] = (float)__ldg(&MB[b000 + o[k]]);
-      }
-      // intensity: lerps along x, y, z, exact at t = 0 and t = 1 so that
-      // quarter turns reproduce the voxels bit for bit
-      float v00 = lerp_exact(v[0], v[1], ax.t), v01 = lerp_exact(v[2], v[3], ax.t);
-      float v10 = lerp_exact(v[4], v[5], ax.t), v11 = lerp_exact(v[6], v[7], ax.t);
-      float v0 = lerp_exact(v00, v01, ay.t), v1 = lerp_exact(v10, v11, ay.t);
-      val = lerp_exact(v0, v1, az.t);
-      // mask decision: same lerp order, round-to-nearest, no contraction
-      float m00 = lerp_rn(mk[0], mk[1], ax.t), m01 = lerp_rn(mk[2], mk[3], ax.t);
-      float m10 = lerp_rn(mk[4], mk[5], ax.t), m11 = lerp_rn(mk[6], mk[7], ax.t);
-      float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
-      float mm = lerp_rn(m0, m1, az.t);
-      m = (mm >= 0.5f) ? 1 : 0;
-    }
+  if (x < g.nx && y < g.ny && z < g.nz) {
+    float val;
+    uint8_t m;
+    resample_voxel(BM, rot[r], g, x, y, z, val, m);
     const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
     Bh[idx] = val;
     Mh[idx] = m;
@@ -92,11 +108,10 @@ k_resample(const float* __restrict__ B, const uint8_t* __restrict__ MB,
   // block reduction of the mask count
   for (int off = 16; off > 0; off >>= 1) count += __shfl_down_sync(0xffffffffu, count, off);
   __shared__ int warp_sums[4];
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) warp_sums[wid] = count;
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     const int c = warp_sums[0] + warp_sums[1] + warp_sums[2] + warp_sums[3];
     if (c) atomicAdd(&msum[r], c);
   }

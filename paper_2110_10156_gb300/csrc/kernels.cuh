@@ -52,10 +52,16 @@ __device__ __forceinline__ unsigned long long make_key(float s, unsigned lin) {
 // Section 3.2: B_hat(x) = B(R (x - c) + c), trilinear; the rotated mask is
 // [trilinear M_B >= 0.5] inside [0, n-1]^3 (+-1e-4).  The sample point and the
 // mask decision use round-to-nearest FP32 operations in a fixed order (no
-// contraction), so the decision is reproducible bit for bit.
-__global__ void k_resample(const float* __restrict__ B, const uint8_t* __restrict__ MB,
-                           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
-                           uint8_t* __restrict__ Mh, int* __restrict__ msum);
+// contraction), so the decision is reproducible bit for bit.  B and M_B are
+// read as (value, mask) pairs prepared by k_pack_bm.
+__global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict__ MB, long long n,
+                          float2* __restrict__ BM);
+__global__ void k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
+                           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum);
+inline dim3 resample_grid(const Geo& g, int nrot) {
+  return dim3((unsigned)((g.nx + 7) / 8), (unsigned)((g.ny + 3) / 4),
+              (unsigned)(((g.nz + 3) / 4) * nrot));
+}
 
 // sum of a uint8 mask (for the fixed volume)
 __global__ void k_mask_sum(const uint8_t* __restrict__ M, long long n, int* __restrict__ out);
