@@ -58,7 +58,9 @@ typedef enum {
   CS_NGF_ENOMEM = 2,      /* device or host allocation failed */
   CS_NGF_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
   CS_NGF_ENOVALID = 4,    /* no rotation had any valid shift */
-  CS_NGF_EUNSUPPORTED = 5 /* FFT length or size not supported */
+  CS_NGF_EUNSUPPORTED = 5, /* FFT length or size not supported */
+  CS_NGF_ECANCELED = 6,    /* a served job was cancelled */
+  CS_NGF_ETIMEOUT = 7      /* a wait ended before the job finished */
 } cs_ngf_status;
 
 typedef struct {
@@ -199,6 +201,68 @@ cs_ngf_status cs_ngf_score_rotations_noalloc(const float* A, const uint8_t* mask
                                              float eps, float gamma, const double* quats,
                                              int32_t R, float* best_score, int32_t* best_shift,
                                              void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop for alignment jobs of mixed
+ * sizes (the scoring of Section 3.2 for each job; the paper runs one job at a
+ * time).  Jobs arrive at any time.  A worker thread admits them in arrival
+ * order while their device footprint fits the memory budget and an active slot
+ * is free.  Device resources are pooled by volume shape and reused without
+ * reallocation.  The fixed-volume spectra of each active job stay resident.
+ * The worker feeds each job's rotations one launch group at a time on the
+ * job's own stream (at most max_inflight groups per job, round-robin over the
+ * active jobs), so work of different jobs overlaps on the GPU.  Each job's
+ * results equal those of cs_ngf_score_rotations on the same inputs and batch.
+ * All inputs of cs_ngf_server_submit are HOST arrays, copied during the call. */
+typedef struct cs_ngf_server cs_ngf_server;
+
+typedef struct {
+  int64_t memory_budget_bytes;      /* device bytes for job resources; 0 = 80 % of free memory */
+  int32_t max_active_jobs;          /* jobs on the GPU at once (default 4) */
+  int32_t max_inflight;             /* launch groups in flight per job (default 2) */
+  int32_t batch;                    /* rotations per launch group when a job's cfg batch is 0 (default 16) */
+  int32_t reserved_;
+  int64_t inject_admission_failure; /* test hook: the job with this id fails admission (ENOMEM); 0 = off */
+} cs_ngf_server_config;
+
+typedef struct {
+  int32_t status;        /* CS_NGF_OK, ENOVALID, ECANCELED or the error that ended the job */
+  int32_t rotations;     /* rotations submitted */
+  int32_t scored;        /* rotations scored (less than rotations if cancelled) */
+  float score;           /* best score over rotations and shifts (-inf if none) */
+  int32_t rot_index;     /* its rotation (-1 if none) */
+  int32_t shift[3];      /* its shift (chi_z, chi_y, chi_x) */
+  double latency_ms;     /* submit to completion */
+  double queue_ms;       /* submit to admission */
+} cs_ngf_job_result;
+
+typedef struct {
+  int32_t pending, active, slots, reserved_;
+  int64_t admitted, completed, bytes_in_use, memory_budget_bytes;
+} cs_ngf_server_info;
+
+void cs_ngf_server_default_config(cs_ngf_server_config* cfg);
+/* Start a server on the current device.  Errors: EINVAL, ENOMEM, ECUDA. */
+cs_ngf_status cs_ngf_server_create(const cs_ngf_server_config* cfg, cs_ngf_server** out);
+/* Queue a job (host arrays A, maskA, B, maskB [nz][ny][nx], quats [R][4]);
+ * cfg (host, NULL = defaults) sets eps, gamma, pad and batch.  A job whose
+ * footprint exceeds the whole budget is refused with ENOMEM. */
+cs_ngf_status cs_ngf_server_submit(cs_ngf_server* s, const float* A, const uint8_t* maskA,
+                                   const float* B, const uint8_t* maskB, const int32_t dims[3],
+                                   const double* quats, int32_t R, const cs_ngf_config* cfg,
+                                   int64_t* job_id);
+/* Ask a job to stop: a pending job never starts, a running job stops after
+ * its launch groups in flight (its result then covers the scored prefix). */
+cs_ngf_status cs_ngf_server_cancel(cs_ngf_server* s, int64_t job_id);
+/* Wait up to timeout_s seconds (negative = no limit) for a job; on return OK
+ * the job's result is in *res (its own status in res->status) and, if not
+ * NULL, its per-rotation results in host best_score [R] / best_shift [R][3];
+ * the job is then forgotten.  ETIMEOUT if it did not finish in time. */
+cs_ngf_status cs_ngf_server_wait(cs_ngf_server* s, int64_t job_id, double timeout_s,
+                                 cs_ngf_job_result* res, float* best_score, int32_t* best_shift);
+cs_ngf_status cs_ngf_server_stats(cs_ngf_server* s, cs_ngf_server_info* info);
+/* Cancel what is left, stop the worker and free every device resource. */
+void cs_ngf_server_destroy(cs_ngf_server* s);
 
 /* Sizes and FFT lengths of a handle.  info: host. */
 cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info);

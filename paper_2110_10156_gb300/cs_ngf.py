@@ -21,7 +21,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-OK, EINVAL, ENOMEM, ECUDA, ENOVALID, EUNSUPPORTED = range(6)
+OK, EINVAL, ENOMEM, ECUDA, ENOVALID, EUNSUPPORTED, ECANCELED, ETIMEOUT = range(8)
 
 EXPORTED = (
     "cs_ngf_default_config", "cs_ngf_prepare_fixed", "cs_ngf_score_rotations",
@@ -29,6 +29,8 @@ EXPORTED = (
     "cs_ngf_get_info", "cs_ngf_release", "cs_ngf_status_string", "cs_ngf_last_error",
     "cs_ngf_auto_pad", "cs_ngf_update_fixed", "cs_ngf_set_profiling", "cs_ngf_stage_times",
     "cs_ngf_launch_count", "cs_ngf_score_rotations_noalloc",
+    "cs_ngf_server_default_config", "cs_ngf_server_create", "cs_ngf_server_submit",
+    "cs_ngf_server_cancel", "cs_ngf_server_wait", "cs_ngf_server_stats", "cs_ngf_server_destroy",
 )
 
 STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "other")
@@ -43,6 +45,24 @@ class Info(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("pad", ctypes.c_int32 * 3),
                 ("batch", ctypes.c_int32), ("sum_mask_a", ctypes.c_int64),
                 ("fixed_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_int64), ("max_active_jobs", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("inject_admission_failure", ctypes.c_int64)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("rotations", ctypes.c_int32), ("scored", ctypes.c_int32),
+                ("score", ctypes.c_float), ("rot_index", ctypes.c_int32), ("shift", ctypes.c_int32 * 3),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int32), ("active", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("memory_budget_bytes", ctypes.c_int64)]
 
 
 _vp, _i32, _p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER
@@ -69,6 +89,19 @@ _lib.cs_ngf_stage_times.argtypes = [_vp, _p(ctypes.c_double), _p(ctypes.c_int64)
 _lib.cs_ngf_score_rotations_noalloc.argtypes = [_vp, _vp, _vp, _vp, _p(_i32), ctypes.c_float,
                                                  ctypes.c_float, _vp, _i32, _vp, _vp, _vp]
 _lib.cs_ngf_score_rotations_noalloc.restype = _i32
+_lib.cs_ngf_server_default_config.argtypes = [_p(ServerConfig)]
+_lib.cs_ngf_server_default_config.restype = None
+_lib.cs_ngf_server_create.argtypes = [_p(ServerConfig), _p(_vp)]
+_lib.cs_ngf_server_submit.argtypes = [_vp, _vp, _vp, _vp, _vp, _p(_i32), _vp, _i32, _p(Config),
+                                      _p(ctypes.c_int64)]
+_lib.cs_ngf_server_cancel.argtypes = [_vp, ctypes.c_int64]
+_lib.cs_ngf_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.c_double, _p(JobResult), _vp, _vp]
+_lib.cs_ngf_server_stats.argtypes = [_vp, _p(ServerInfo)]
+_lib.cs_ngf_server_destroy.argtypes = [_vp]
+_lib.cs_ngf_server_destroy.restype = None
+for _name in ("cs_ngf_server_create", "cs_ngf_server_submit", "cs_ngf_server_cancel",
+              "cs_ngf_server_wait", "cs_ngf_server_stats"):
+    getattr(_lib, _name).restype = _i32
 _lib.cs_ngf_launch_count.argtypes = []
 _lib.cs_ngf_launch_count.restype = ctypes.c_int64
 for _name in ("cs_ngf_update_fixed", "cs_ngf_set_profiling", "cs_ngf_stage_times",
@@ -303,6 +336,86 @@ def score_rotations_noalloc(A, MA, B, MB, quats, eps=1e-5, gamma=0.5, out_score=
         _dev_ptr(out_shift, torch.int32, "best_shift"), _stream_ptr(stream)),
         "cs_ngf_score_rotations_noalloc")
     return out_score, out_shift
+
+
+class Server:
+    """Continuous-batching request loop (cs_ngf_server_*): submit host arrays,
+    wait for per-job results.  Runs on the current CUDA device."""
+
+    def __init__(self, memory_budget_bytes=0, max_active_jobs=4, max_inflight=2, batch=16,
+                 inject_admission_failure=0):
+        cfg = ServerConfig()
+        _lib.cs_ngf_server_default_config(ctypes.byref(cfg))
+        cfg.memory_budget_bytes = int(memory_budget_bytes)
+        cfg.max_active_jobs = int(max_active_jobs)
+        cfg.max_inflight = int(max_inflight)
+        cfg.batch = int(batch)
+        cfg.inject_admission_failure = int(inject_admission_failure)
+        h = ctypes.c_void_p()
+        _check(_lib.cs_ngf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cs_ngf_server_create")
+        self._h = h
+        self._R = {}
+
+    def submit(self, A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, batch=0) -> int:
+        arrs = []
+        for name, a, dt in (("A", A, np.float32), ("maskA", MA, np.uint8), ("B", B, np.float32),
+                            ("maskB", MB, np.uint8)):
+            a = np.ascontiguousarray(a, dtype=dt)
+            if a.ndim != 3 or a.shape != tuple(np.shape(A)):
+                raise ValueError(f"{name} must be 3-D with A's shape")
+            arrs.append(a)
+        q = _quats(quats)
+        cfg = Config()
+        _lib.cs_ngf_default_config(ctypes.byref(cfg))
+        cfg.eps, cfg.gamma, cfg.batch = float(eps), float(gamma), int(batch)
+        if pad is not None:
+            for i, p in enumerate(pad):
+                cfg.pad[i] = int(p)
+        dims = (ctypes.c_int32 * 3)(*arrs[0].shape)
+        jid = ctypes.c_int64()
+        _check(_lib.cs_ngf_server_submit(self._h, *[ctypes.c_void_p(a.ctypes.data) for a in arrs], dims,
+                                         q.ctypes.data_as(ctypes.c_void_p), q.shape[0], ctypes.byref(cfg),
+                                         ctypes.byref(jid)), "cs_ngf_server_submit")
+        self._R[jid.value] = q.shape[0]
+        return int(jid.value)
+
+    def cancel(self, job: int):
+        _check(_lib.cs_ngf_server_cancel(self._h, int(job)), "cs_ngf_server_cancel")
+
+    def wait(self, job: int, timeout_s: float = -1.0, per_rotation: bool = True):
+        """dict with status, score, rot_index, shift, latency_ms, queue_ms and,
+        if per_rotation, the per-rotation scores [R] and shifts [R, 3]."""
+        R = self._R.get(int(job), 0)
+        res = JobResult()
+        sc = np.full(R, -np.inf, np.float32) if per_rotation else None
+        sh = np.zeros((R, 3), np.int32) if per_rotation else None
+        _check(_lib.cs_ngf_server_wait(self._h, int(job), float(timeout_s), ctypes.byref(res),
+                                       ctypes.c_void_p(sc.ctypes.data) if per_rotation else None,
+                                       ctypes.c_void_p(sh.ctypes.data) if per_rotation else None),
+               "cs_ngf_server_wait")
+        self._R.pop(int(job), None)
+        out = dict(status=int(res.status), rotations=int(res.rotations), scored=int(res.scored),
+                   score=float(res.score), rot_index=int(res.rot_index), shift=tuple(res.shift),
+                   latency_ms=float(res.latency_ms), queue_ms=float(res.queue_ms))
+        if per_rotation:
+            out["scores"], out["shifts"] = sc[: res.scored], sh[: res.scored]
+        return out
+
+    def stats(self):
+        info = ServerInfo()
+        _check(_lib.cs_ngf_server_stats(self._h, ctypes.byref(info)), "cs_ngf_server_stats")
+        return {f: getattr(info, f) for f, _ in ServerInfo._fields_ if f != "reserved_"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cs_ngf_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def prepare_fixed(A, MA, **kw) -> Fixed:

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/cs_ngf.h"
+#include "handle.h"
 #include "kernels.cuh"
 
 using namespace csngf;
@@ -22,14 +23,17 @@ thread_local std::string g_last_error;
 namespace csngf {
 // lets other translation units of the library report through cs_ngf_last_error
 void set_last_error(const std::string& msg) { g_last_error = msg; }
-}  // namespace csngf
-
-namespace {
-
+namespace detail {
 cs_ngf_status fail(cs_ngf_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
 }
+}  // namespace detail
+}  // namespace csngf
+
+using csngf::detail::fail;
+
+namespace {
 
 #define CS_CUDA(call)                                                                      \
   do {                                                                                     \
@@ -99,40 +103,6 @@ cudaError_t dalloc(T** p, size_t count) {
 
 }  // namespace
 
-struct cs_ngf_fixed {
-  int device = 0;
-  Geo g{};
-  float eps = 1e-5f, gamma = 0.5f;
-  int batch = 1;
-  int sumA = 0;
-  size_t f02_elems = 0, f13_elems = 0;
-  float2* UV = nullptr;
-  float* Bh = nullptr;
-  uint8_t* Mh = nullptr;
-  float2* BM = nullptr;        // (B, mask) pairs of the current call
-  float2* F02 = nullptr;
-  float2* F13 = nullptr;
-  int* msum = nullptr;
-  float* thr = nullptr;
-  unsigned long long* keys = nullptr;
-  float2* tw[3] = {nullptr, nullptr, nullptr};   // z, y, x
-  // rotation matrices: pinned host staging + device copy, grown on demand
-  RotMat* rot_h = nullptr;
-  RotMat* rot_d = nullptr;
-  int rot_cap = 0;
-  cudaEvent_t rot_ev = nullptr;
-  // host-buffer entry point staging
-  float* stage_B = nullptr;
-  uint8_t* stage_M = nullptr;
-  float* res_score = nullptr;
-  int32_t* res_shift = nullptr;
-  int res_cap = 0;
-  size_t fixed_bytes = 0, workspace_bytes = 0;
-  // per-stage CUDA-event timing (cs_ngf_set_profiling)
-  bool profiling = false;
-  struct Span { int stage; cudaEvent_t a, b; };
-  std::vector<Span> spans;
-};
 
 namespace {
 
@@ -149,7 +119,7 @@ struct Stage {
     if (f->profiling && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
   }
   ~Stage() {
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!f->capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
     if (a) {
       cudaEvent_t b = nullptr;
       if (cudaEventCreate(&b) == cudaSuccess) {
@@ -203,6 +173,10 @@ void free_handle(cs_ngf_fixed* f) {
   }
   if (f->rot_ev) cudaEventSynchronize(f->rot_ev);
   for (auto& sp : f->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+  if (f->gexec) cudaGraphExecDestroy(f->gexec);
+  cudaFree(f->rot_slot);
+  cudaFree(f->slot_score);
+  cudaFree(f->slot_shift);
   cudaFreeHost(f->rot_h);
   cudaFree(f->rot_d);
   if (f->rot_ev) cudaEventDestroy(f->rot_ev);
@@ -280,16 +254,16 @@ cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, 
   return check_launch("pack");
 }
 
-// score rotations [r0, r0 + nb) whose matrices are at f->rot_d + r0, with the
-// floating volume already packed in f->BM
-cs_ngf_status score_batch(cs_ngf_fixed* f, int r0, int nb,
-                          float* best_score, int32_t* best_shift, float* map, cudaStream_t st) {
+// score nb rotations whose matrices are at rot (device), with the floating
+// volume already packed in f->BM; results to out_score[nb], out_shift[nb][3]
+cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float* out_score,
+                               int32_t* out_shift, float* map, cudaStream_t st) {
   const Geo& g = f->g;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int) * nb, st));
   CS_CUDA(cudaMemsetAsync(f->keys, 0, sizeof(unsigned long long) * nb, st));
   {
     Stage sp(f, 0, st);
-    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, f->rot_d + r0, g, f->Bh, f->Mh, f->msum);
+    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, rot, g, f->Bh, f->Mh, f->msum);
   }
   if (cs_ngf_status s = check_launch("resample")) return s;
   const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
@@ -301,10 +275,47 @@ cs_ngf_status score_batch(cs_ngf_fixed* f, int r0, int nb,
   if (cs_ngf_status s = run_transforms(f, nb, map, st)) return s;
   {
     Stage sp(f, 7, st);
-    k_finalize<<<(nb + 127) / 128, 128, 0, st>>>(f->keys, nb, g, best_score + r0,
-                                                  best_shift + 3 * (size_t)r0);
+    k_finalize<<<(nb + 127) / 128, 128, 0, st>>>(f->keys, nb, g, out_score, out_shift);
   }
   return check_launch("finalize");
+}
+
+constexpr int kKernelsPerBatch = 8;   // resample, thresholds, 5 passes, finalize
+
+cs_ngf_status score_batch(cs_ngf_fixed* f, int r0, int nb, float* best_score, int32_t* best_shift,
+                          float* map, cudaStream_t st) {
+  return score_batch_ptrs(f, f->rot_d + r0, nb, best_score + r0, best_shift + 3 * (size_t)r0, map, st);
+}
+
+// capture the full-batch launch sequence once (on a private stream; the
+// graph is then replayed on the caller's stream)
+cs_ngf_status ensure_graph(cs_ngf_fixed* f) {
+  if (f->gexec) return CS_NGF_OK;
+  if (!f->rot_slot) {
+    CS_CUDA(dalloc(&f->rot_slot, (size_t)f->batch));
+    CS_CUDA(dalloc(&f->slot_score, (size_t)f->batch));
+    CS_CUDA(dalloc(&f->slot_shift, (size_t)f->batch * 3));
+  }
+  cudaStream_t cs = nullptr;
+  CS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  cs_ngf_status st = CS_NGF_OK;
+  if (e == cudaSuccess) {
+    f->capturing = true;
+    st = score_batch_ptrs(f, f->rot_slot, f->batch, f->slot_score, f->slot_shift, nullptr, cs);
+    f->capturing = false;
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  if (e == cudaSuccess && st == CS_NGF_OK) e = cudaGraphInstantiate(&f->gexec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (st != CS_NGF_OK) return st;
+  if (e != cudaSuccess) {
+    f->gexec = nullptr;
+    return fail(CS_NGF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  return CS_NGF_OK;
 }
 
 // Section 3.1 A side: NGF channels of A times M_A, forward FFTs, weights -> f->UV
@@ -324,6 +335,10 @@ cs_ngf_status run_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* MA, cuda
   int sumA = 0;
   CS_CUDA(cudaMemcpyAsync(&sumA, f->msum, sizeof(int), cudaMemcpyDeviceToHost, st));
   CS_CUDA(cudaStreamSynchronize(st));
+  if (f->gexec && sumA != f->sumA) {     // the captured threshold launch holds sum(M_A)
+    cudaGraphExecDestroy(f->gexec);
+    f->gexec = nullptr;
+  }
   f->sumA = sumA;
   return CS_NGF_OK;
 }
@@ -334,17 +349,69 @@ cs_ngf_status check_volume_args(const cs_ngf_fixed* f, const float* B, const uin
   return CS_NGF_OK;
 }
 
+// rotations [r0_begin, r0_begin + n) of the uploaded set; full launch groups
+// replay the captured graph, a short tail is launched directly
+cs_ngf_status score_range_impl(cs_ngf_fixed* f, int r0_begin, int n, float* best_score,
+                               int32_t* best_shift, cudaStream_t st) {
+  const int end = r0_begin + n;
+  for (int r0 = r0_begin; r0 < end; r0 += f->batch) {
+    const int nb = std::min(f->batch, end - r0);
+    if (nb == f->batch && !f->profiling) {
+      if (cs_ngf_status s = ensure_graph(f)) return s;
+      CS_CUDA(cudaMemcpyAsync(f->rot_slot, f->rot_d + r0, sizeof(RotMat) * nb, cudaMemcpyDeviceToDevice, st));
+      CS_CUDA(cudaGraphLaunch(f->gexec, st));
+      CS_CUDA(cudaMemcpyAsync(best_score + r0, f->slot_score, sizeof(float) * nb, cudaMemcpyDeviceToDevice, st));
+      CS_CUDA(cudaMemcpyAsync(best_shift + 3 * (size_t)r0, f->slot_shift, sizeof(int32_t) * 3 * nb,
+                              cudaMemcpyDeviceToDevice, st));
+      g_launches.fetch_add(kKernelsPerBatch, std::memory_order_relaxed);
+    } else if (cs_ngf_status s = score_batch(f, r0, nb, best_score, best_shift, nullptr, st)) {
+      return s;
+    }
+  }
+  return CS_NGF_OK;
+}
+
 cs_ngf_status score_all(cs_ngf_fixed* f, const float* B, const uint8_t* MB, const double* quats,
                         int R, float* best_score, int32_t* best_shift, cudaStream_t st) {
   if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
   if (!best_score || !best_shift) return fail(CS_NGF_EINVAL, "output pointer is NULL");
   if (cs_ngf_status s = upload_rotations(f, quats, R, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, MB, st)) return s;
-  for (int r0 = 0; r0 < R; r0 += f->batch) {
-    const int nb = std::min(f->batch, R - r0);
-    if (cs_ngf_status s = score_batch(f, r0, nb, best_score, best_shift, nullptr, st)) return s;
+  return score_range_impl(f, 0, R, best_score, best_shift, st);
+}
+
+cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 2 || dims[a] > 256)
+      return fail(CS_NGF_EINVAL, "dims must be in [2, 256], got " + std::to_string(dims[a]));
+  if (!(cfg.eps > 0.0f) || !std::isfinite(cfg.eps)) return fail(CS_NGF_EINVAL, "eps must be > 0");
+  if (!(cfg.gamma > 0.0f && cfg.gamma <= 1.0f)) return fail(CS_NGF_EINVAL, "gamma must be in (0, 1]");
+  if (cfg.batch < 0) return fail(CS_NGF_EINVAL, "batch must be >= 0");
+  for (int a = 0; a < 3; ++a) {
+    pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
+    if (!pad_supported(pad[a]))
+      return fail(CS_NGF_EUNSUPPORTED, "FFT length " + std::to_string(pad[a]) + " not supported");
+    if (pad[a] < 2 * dims[a] - 1)
+      return fail(CS_NGF_EINVAL, "FFT length " + std::to_string(pad[a]) + " < 2n-1");
   }
   return CS_NGF_OK;
+}
+
+struct Sizes {
+  size_t f02_elems, f13_elems, per_rot, shared_ws, uv_elems;
+};
+
+Sizes sizes_for(const int32_t dims[3], const int pad[3]) {
+  const size_t nz = dims[0], ny = dims[1], nx = dims[2];
+  const size_t Pz = pad[0], Py = pad[1], Px = pad[2];
+  const size_t vz = 2 * nz - 1, vy = 2 * ny - 1, nvox = nz * ny * nx;
+  Sizes z;
+  z.f02_elems = std::max(4 * nz * ny * Px, vz * Px * Py);
+  z.f13_elems = std::max(4 * nz * Px * Py, vz * vy * Px);
+  z.per_rot = (z.f02_elems + z.f13_elems) * sizeof(float2) + nvox * 5;
+  z.shared_ws = nvox * sizeof(float2);
+  z.uv_elems = 7 * (Px / 2 + 1) * Py * Pz;
+  return z;
 }
 
 cs_ngf_status ensure_results(cs_ngf_fixed* f, int R) {
@@ -362,6 +429,34 @@ cs_ngf_status ensure_results(cs_ngf_fixed* f, int R) {
 }
 
 }  // namespace
+
+namespace csngf {
+namespace detail {
+cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* q, int R, cudaStream_t st) {
+  return ::upload_rotations(f, q, R, st);
+}
+cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st) {
+  return ::pack_floating(f, B, MB, st);
+}
+cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int32_t* best_shift,
+                          cudaStream_t st) {
+  return ::score_range_impl(f, r0, n, best_score, best_shift, st);
+}
+cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
+  return ::resolve_pads_impl(dims, cfg, pad);
+}
+size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch) {
+  const Sizes z = ::sizes_for(dims, pad);
+  int distinct = 1;
+  if (pad[1] != pad[0]) ++distinct;
+  if (pad[2] != pad[0] && pad[2] != pad[1]) ++distinct;
+  size_t tw = 0;
+  for (int a = 0; a < 3; ++a) tw += (size_t)pad[a] * sizeof(float2);
+  return z.uv_elems * sizeof(float2) + (size_t)batch * z.per_rot + z.shared_ws +
+         (size_t)batch * (sizeof(int) + sizeof(float) + sizeof(unsigned long long)) + tw + (size_t)distinct * 0;
+}
+}  // namespace detail
+}  // namespace csngf
 
 // ============================================================================
 extern "C" {
@@ -383,6 +478,8 @@ const char* cs_ngf_status_string(int32_t s) {
     case CS_NGF_ECUDA: return "CUDA error";
     case CS_NGF_ENOVALID: return "no valid shift for any rotation";
     case CS_NGF_EUNSUPPORTED: return "unsupported size";
+    case CS_NGF_ECANCELED: return "cancelled";
+    case CS_NGF_ETIMEOUT: return "timed out";
     default: return "unknown status";
   }
 }
@@ -398,20 +495,8 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   cs_ngf_config cfg;
   cs_ngf_default_config(&cfg);
   if (cfg_in) cfg = *cfg_in;
-  for (int a = 0; a < 3; ++a)
-    if (dims[a] < 2 || dims[a] > 256)
-      return fail(CS_NGF_EINVAL, "dims must be in [2, 256], got " + std::to_string(dims[a]));
-  if (!(cfg.eps > 0.0f) || !std::isfinite(cfg.eps)) return fail(CS_NGF_EINVAL, "eps must be > 0");
-  if (!(cfg.gamma > 0.0f && cfg.gamma <= 1.0f)) return fail(CS_NGF_EINVAL, "gamma must be in (0, 1]");
-  if (cfg.batch < 0) return fail(CS_NGF_EINVAL, "batch must be >= 0");
   int pad[3];
-  for (int a = 0; a < 3; ++a) {
-    pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
-    if (!pad_supported(pad[a]))
-      return fail(CS_NGF_EUNSUPPORTED, "FFT length " + std::to_string(pad[a]) + " not supported");
-    if (pad[a] < 2 * dims[a] - 1)
-      return fail(CS_NGF_EINVAL, "FFT length " + std::to_string(pad[a]) + " < 2n-1");
-  }
+  if (cs_ngf_status s = resolve_pads_impl(dims, cfg, pad)) return s;
 
   cs_ngf_fixed* f = new (std::nothrow) cs_ngf_fixed();
   if (!f) return fail(CS_NGF_ENOMEM, "host allocation failed");
@@ -425,13 +510,10 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   g.eps2 = cfg.eps * cfg.eps;
   g.nvox = (long long)g.nz * g.ny * g.nx;
 
-  const size_t f0 = (size_t)4 * g.nz * g.ny * g.Px, f2 = (size_t)g.vz * g.Px * g.Py;
-  const size_t f1 = (size_t)4 * g.nz * g.Px * g.Py, f3 = (size_t)g.vz * g.vy * g.Px;
-  f->f02_elems = std::max(f0, f2);
-  f->f13_elems = std::max(f1, f3);
-  const size_t per_rot = (f->f02_elems + f->f13_elems) * sizeof(float2) + (size_t)g.nvox * 5;
-  const size_t shared_ws = (size_t)g.nvox * sizeof(float2);
-  const size_t uv_elems = (size_t)7 * (g.Px / 2 + 1) * g.Py * g.Pz;
+  const Sizes sz = sizes_for(dims, pad);
+  f->f02_elems = sz.f02_elems;
+  f->f13_elems = sz.f13_elems;
+  const size_t per_rot = sz.per_rot, shared_ws = sz.shared_ws, uv_elems = sz.uv_elems;
   int batch = cfg.batch;
   if (batch == 0) {
     size_t free_b = 0, total_b = 0;

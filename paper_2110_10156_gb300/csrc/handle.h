@@ -1,0 +1,76 @@
+// Internal view of the library's handle, shared by its translation units
+// (the C ABI only exposes it as an opaque pointer).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cs_ngf.h"
+#include "kernels.cuh"
+
+struct cs_ngf_fixed {
+  using Geo = csngf::Geo;
+  using RotMat = csngf::RotMat;
+  int device = 0;
+  Geo g{};
+  float eps = 1e-5f, gamma = 0.5f;
+  int batch = 1;
+  int sumA = 0;
+  size_t f02_elems = 0, f13_elems = 0;
+  float2* UV = nullptr;
+  float* Bh = nullptr;
+  uint8_t* Mh = nullptr;
+  float2* BM = nullptr;        // (B, mask) pairs of the current call
+  float2* F02 = nullptr;
+  float2* F13 = nullptr;
+  int* msum = nullptr;
+  float* thr = nullptr;
+  unsigned long long* keys = nullptr;
+  float2* tw[3] = {nullptr, nullptr, nullptr};   // z, y, x
+  // rotation matrices: pinned host staging + device copy, grown on demand
+  RotMat* rot_h = nullptr;
+  RotMat* rot_d = nullptr;
+  int rot_cap = 0;
+  cudaEvent_t rot_ev = nullptr;
+  // host-buffer entry point staging
+  float* stage_B = nullptr;
+  uint8_t* stage_M = nullptr;
+  float* res_score = nullptr;
+  int32_t* res_shift = nullptr;
+  int res_cap = 0;
+  size_t fixed_bytes = 0, workspace_bytes = 0;
+  // one captured CUDA graph for a full batch, replayed per batch; the batch's
+  // rotation matrices and results go through fixed slots
+  cudaGraphExec_t gexec = nullptr;
+  RotMat* rot_slot = nullptr;
+  float* slot_score = nullptr;
+  int32_t* slot_shift = nullptr;
+  bool capturing = false;
+  // per-stage CUDA-event timing (cs_ngf_set_profiling); disables graph replay
+  bool profiling = false;
+  struct Span { int stage; cudaEvent_t a, b; };
+  std::vector<Span> spans;
+};
+
+namespace csngf {
+namespace detail {
+
+// record the calling thread's error detail (cs_ngf_last_error) and return s
+cs_ngf_status fail(cs_ngf_status s, const std::string& msg);
+// host FP64 quaternions -> FP32 matrices in f->rot_d[0..R)
+cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* quats, int R, cudaStream_t st);
+// (B, M_B) -> f->BM for the following score calls
+cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st);
+// score rotations [r0, r0 + n) of the uploaded set into best_score / best_shift
+// (device, indexed from r0), in launch groups of f->batch
+cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int32_t* best_shift,
+                          cudaStream_t st);
+// validate dims / cfg and return the FFT lengths; EINVAL / EUNSUPPORTED on error
+cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]);
+// device bytes a handle of these dims, FFT lengths and batch allocates
+size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch);
+
+}  // namespace detail
+}  // namespace csngf
