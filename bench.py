@@ -124,18 +124,19 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ byte model
-def stage_bytes(dims, pad, nb, stage):
-    """Algorithmic HBM bytes of one launch that scores nb rotations."""
+def stage_bytes(dims, pad, nb, stage, nf=4):
+    """Algorithmic HBM bytes of one launch that scores nb rotations (nf packed
+    fields per rotation: 4 for the squared measure)."""
     nz, ny, nx = dims
     Pz, Py, Px = pad
     vz, vy = 2 * nz - 1, 2 * ny - 1
     nvox = nz * ny * nx
     c8 = 8
-    F0 = 4 * nz * ny * Px * c8
-    F1 = 4 * nz * Px * Py * c8
+    F0 = nf * nz * ny * Px * c8
+    F1 = nf * nz * Px * Py * c8
     F2 = vz * Px * Py * c8
     F3 = vz * vy * Px * c8
-    UV = 7 * (Px // 2 + 1) * Py * Pz * c8
+    UV = (2 * nf - 1) * (Px // 2 + 1) * Py * Pz * c8
     return {
         "resample": nvox * 5 + nb * nvox * 5,
         "fwd_x": nb * (nvox * 5 + F0),
@@ -479,6 +480,45 @@ def run_large(args):
     return 0
 
 
+def run_tab3(args):
+    """One all-shift CSNGF evaluation on cube pairs of side 8..128 (both
+    volumes' transforms, the sum in the spectrum, the inverse, the
+    normalisation and the argmax): GPU path time, and the CPU direct
+    algorithm (Section 5.2) timed where it finishes in seconds."""
+    import torch
+    from oracle import cs_ngf_oracle as O
+    from paper_2110_10156_gb300 import cs_ngf, synth
+    rows = []
+    ident = np.array([[1.0, 0.0, 0.0, 0.0]])
+    for n in (8, 16, 32, 64, 128):
+        p = synth.small_pair(500 + n, (n, n, n), n_rot=1, masks="full")
+        A, MA, B, MB = (_dev(getattr(p, k)) for k in ("A", "MA", "B", "MB"))
+        f = cs_ngf.prepare_fixed(A, MA, batch=1)
+        for _ in range(5):
+            f.update_fixed(A, MA)
+            f.align(B, MB, ident)
+        ts = []
+        for _ in range(20):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f.update_fixed(A, MA)
+            f.align(B, MB, ident)
+            ts.append(time.perf_counter() - t0)
+        gpu = float(np.median(ts))
+        cpu = None
+        if n <= args.tab3_direct_max:
+            t0 = time.perf_counter()
+            O.csngf_direct(p.A, p.MA, p.B, p.MB, 1e-5, 0.5)
+            cpu = time.perf_counter() - t0
+        rows.append({"side": n, "fft": list(f.pad), "gpu_s": gpu, "cpu_direct_s": cpu,
+                     "speedup": None if cpu is None else cpu / gpu})
+        f.release()
+    print(json.dumps({"metric": "one all-shift CSNGF evaluation vs side (Tab. 3 workload)", "unit": "s",
+                      "rows": rows, "dtype": "f32 (GPU) / f64 (CPU direct)", "data": "synthetic cubes"}),
+          flush=True)
+    return 0
+
+
 SERVE_SHAPES = ((64, 64, 64), (96, 128, 128), (150, 150, 150), (192, 192, 160))
 
 
@@ -559,7 +599,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=16,
                     help="oracle rotations per CPU step (at most one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("align150", "small32", "serve", "large256"),
+    ap.add_argument("--tab3-direct-max", type=int, default=16)
+    ap.add_argument("--workload", choices=("align150", "small32", "serve", "large256", "tab3"),
                     default="align150", help="align150 is the headline line; the others print "
                                               "their own metrics")
     ap.add_argument("--serve-jobs", type=int, default=24)
@@ -570,7 +611,8 @@ def main():
     if args.impl == "ours" and args.workload != "align150":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        return {"small32": run_small_latency, "serve": run_serving, "large256": run_large}[args.workload](args)
+        return {"small32": run_small_latency, "serve": run_serving, "large256": run_large,
+                "tab3": run_tab3}[args.workload](args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

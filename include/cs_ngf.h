@@ -63,11 +63,17 @@ typedef enum {
   CS_NGF_ETIMEOUT = 7      /* a wait ended before the job finished */
 } cs_ngf_status;
 
+typedef enum {
+  CS_NGF_SQUARED = 0,   /* s_NGF = <n_A, n_B>^2 (Eq. 2), the paper's CSNGF */
+  CS_NGF_UNSQUARED = 1  /* s_US-NGF = <n_A, n_B> (Eq. 3), the USNGF method of Section 5.1 */
+} cs_ngf_measure;
+
 typedef struct {
   float eps;        /* Eq. 1 regulariser; the paper uses 1e-5 */
   float gamma;      /* minimum overlap fraction in (0, 1]; the paper uses 0.5 */
   int32_t pad[3];   /* FFT lengths (z, y, x); 0 = automatic */
   int32_t batch;    /* rotations per launch group; 0 = automatic (memory-sized) */
+  int32_t measure;  /* cs_ngf_measure; default CS_NGF_SQUARED */
 } cs_ngf_config;
 
 typedef struct {

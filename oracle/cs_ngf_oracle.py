@@ -50,6 +50,7 @@ F32 = np.float32
 # channel order of Eq. 6: (xx, yy, zz, xy, xz, yz); cross terms carry weight 2
 CHANNEL_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
 CHANNEL_WEIGHTS = (1.0, 1.0, 1.0, 2.0, 2.0, 2.0)
+MEASURES = ("squared", "unsquared")
 
 SUPPORTED_PADS = (16, 32, 64, 128, 160, 200, 256, 320, 400, 512)
 
@@ -181,17 +182,25 @@ def ngf(V: np.ndarray, eps: float):
     return gx * inv, gy * inv, gz * inv
 
 
-def s_ngf(nA, nB):
-    """Eq. 2: squared dot product of two NGF vectors (voxel-wise)."""
+def s_ngf(nA, nB, measure="squared"):
+    """Eq. 2 (squared dot product of two NGF vectors, voxel-wise) or Eq. 3
+    (the plain dot product) for measure="unsquared"."""
     d = nA[0] * nB[0] + nA[1] * nB[1] + nA[2] * nB[2]
-    return d * d
+    return d * d if measure == "squared" else d
 
 
-def channels(V: np.ndarray, M: np.ndarray, eps: float):
-    """Eq. 6 channels times the mask: M * (nx^2, ny^2, nz^2, nx ny, nx nz, ny nz)."""
+def channels(V: np.ndarray, M: np.ndarray, eps: float, measure="squared"):
+    """Eq. 6 channels times the mask, M * (nx^2, ny^2, nz^2, nx ny, nx nz, ny nz),
+    or for Eq. 3 the three components M * (nx, ny, nz)."""
     n = ngf(V, eps)
     m = np.asarray(M, dtype=np.float64)
+    if measure == "unsquared":
+        return [m * n[i] for i in range(3)]
     return [m * n[i] * n[j] for (i, j) in CHANNEL_PAIRS]
+
+
+def channel_weights(measure="squared"):
+    return CHANNEL_WEIGHTS if measure == "squared" else (1.0, 1.0, 1.0)
 
 
 def overlap_threshold(sumA: int, sumB: int, gamma: float) -> int:
@@ -214,7 +223,7 @@ def _shift_slices(chi, dims_a, dims_b):
     return tuple(sa), tuple(sb)
 
 
-def csngf_direct(A, MA, Bhat, Mhat, eps, gamma, chis=None):
+def csngf_direct(A, MA, Bhat, Mhat, eps, gamma, chis=None, measure="squared"):
     """Eq. 5 evaluated shift by shift: returns (score map, overlap map).
 
     The maps cover chi in [-(n-1), n-1] per axis (array index chi + n - 1);
@@ -245,7 +254,8 @@ def csngf_direct(A, MA, Bhat, Mhat, eps, gamma, chis=None):
         if N < thr:
             continue
         d = nA[0][sa] * nB[0][sb] + nA[1][sa] * nB[1][sb] + nA[2][sa] * nB[2][sb]
-        score[idx] = float((w * d * d).sum()) / N
+        val = d * d if measure == "squared" else d
+        score[idx] = float((w * val).sum()) / N
     return score, count
 
 
@@ -266,17 +276,18 @@ def _gather_shifts(c, dims, pad):
     return c[np.ix_(*idx)]
 
 
-def csngf_fft(A, MA, Bhat, Mhat, eps, gamma, pad=None):
+def csngf_fft(A, MA, Bhat, Mhat, eps, gamma, pad=None, measure="squared"):
     """Eq. 6-8: six weighted channel correlations summed in the spectrum, one
-    inverse FFT, divided by the mask correlation N (Eq. 5)."""
+    inverse FFT, divided by the mask correlation N (Eq. 5).  With
+    measure="unsquared" the three Eq. 3 component correlations instead."""
     dims = A.shape
     if pad is None:
         pad = tuple(auto_pad(n) for n in dims)
     pad = tuple(int(p) for p in pad)
-    a = channels(A, MA, eps)
-    b = channels(Bhat, Mhat, eps)
+    a = channels(A, MA, eps, measure)
+    b = channels(Bhat, Mhat, eps, measure)
     acc = None
-    for w, ac, bc in zip(CHANNEL_WEIGHTS, a, b):
+    for w, ac, bc in zip(channel_weights(measure), a, b):
         term = w * np.conj(np.fft.rfftn(ac, s=pad, axes=(0, 1, 2))) * np.fft.rfftn(bc, s=pad, axes=(0, 1, 2))
         acc = term if acc is None else acc + term
     X = _gather_shifts(np.fft.irfftn(acc, s=pad, axes=(0, 1, 2)), dims, pad)
@@ -303,19 +314,20 @@ def best_of_map(score):
     return float(score[idx]), chi
 
 
-def score_map(A, MA, B, MB, q, eps=1e-5, gamma=0.5, pad=None, form="fft"):
+def score_map(A, MA, B, MB, q, eps=1e-5, gamma=0.5, pad=None, form="fft", measure="squared"):
     """Full score map for one rotation q (Section 3.2 then Eq. 5)."""
     Bhat, Mhat = resample(B, MB, q)
     if form == "direct":
-        return csngf_direct(A, MA, Bhat, Mhat, eps, gamma)
-    return csngf_fft(A, MA, Bhat, Mhat, eps, gamma, pad)
+        return csngf_direct(A, MA, Bhat, Mhat, eps, gamma, measure=measure)
+    return csngf_fft(A, MA, Bhat, Mhat, eps, gamma, pad, measure=measure)
 
 
-def score_rotations(A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, form="fft"):
+def score_rotations(A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, form="fft",
+                    measure="squared"):
     """Per rotation: best score over chi and its shift (z, y, x)."""
     scores, shifts = [], []
     for q in quats:
-        s, _ = score_map(A, MA, B, MB, q, eps, gamma, pad, form)
+        s, _ = score_map(A, MA, B, MB, q, eps, gamma, pad, form, measure)
         b, chi = best_of_map(s)
         scores.append(b)
         shifts.append(chi)

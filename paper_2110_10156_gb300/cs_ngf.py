@@ -38,7 +38,10 @@ STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "othe
 
 class Config(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("gamma", ctypes.c_float),
-                ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32)]
+                ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32), ("measure", ctypes.c_int32)]
+
+
+MEASURES = {"squared": 0, "unsquared": 1}
 
 
 class Info(ctypes.Structure):
@@ -162,7 +165,8 @@ def _quats(q) -> np.ndarray:
 class Fixed:
     """Handle on the device-resident fixed-volume spectra (cs_ngf_prepare_fixed)."""
 
-    def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None):
+    def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None,
+                 measure="squared"):
         import torch
         if A.dim() != 3:
             raise ValueError("A must be [nz][ny][nx]")
@@ -177,6 +181,8 @@ class Fixed:
             for i, p in enumerate(pad):
                 cfg.pad[i] = int(p)
         cfg.batch = int(batch)
+        cfg.measure = MEASURES[measure]
+        self.measure = measure
         dims = (ctypes.c_int32 * 3)(*self.dims)
         h = ctypes.c_void_p()
         st = _check(_lib.cs_ngf_prepare_fixed(_dev_ptr(A, torch.float32, "A"),
@@ -356,7 +362,8 @@ class Server:
         self._h = h
         self._R = {}
 
-    def submit(self, A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, batch=0) -> int:
+    def submit(self, A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, batch=0,
+               measure="squared") -> int:
         arrs = []
         for name, a, dt in (("A", A, np.float32), ("maskA", MA, np.uint8), ("B", B, np.float32),
                             ("maskB", MB, np.uint8)):
@@ -368,6 +375,7 @@ class Server:
         cfg = Config()
         _lib.cs_ngf_default_config(ctypes.byref(cfg))
         cfg.eps, cfg.gamma, cfg.batch = float(eps), float(gamma), int(batch)
+        cfg.measure = MEASURES[measure]
         if pad is not None:
             for i, p in enumerate(pad):
                 cfg.pad[i] = int(p)

@@ -387,6 +387,8 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
   if (!(cfg.eps > 0.0f) || !std::isfinite(cfg.eps)) return fail(CS_NGF_EINVAL, "eps must be > 0");
   if (!(cfg.gamma > 0.0f && cfg.gamma <= 1.0f)) return fail(CS_NGF_EINVAL, "gamma must be in (0, 1]");
   if (cfg.batch < 0) return fail(CS_NGF_EINVAL, "batch must be >= 0");
+  if (cfg.measure != CS_NGF_SQUARED && cfg.measure != CS_NGF_UNSQUARED)
+    return fail(CS_NGF_EINVAL, "unknown measure");
   for (int a = 0; a < 3; ++a) {
     pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
     if (!pad_supported(pad[a]))
@@ -401,16 +403,21 @@ struct Sizes {
   size_t f02_elems, f13_elems, per_rot, shared_ws, uv_elems;
 };
 
-Sizes sizes_for(const int32_t dims[3], const int pad[3]) {
+// channel fields per measure: three packed pairs of Eq. 6 products, or two of
+// the Eq. 3 components; the mask field comes on top
+int channel_fields(int measure) { return measure == CS_NGF_UNSQUARED ? 2 : 3; }
+
+Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure) {
   const size_t nz = dims[0], ny = dims[1], nx = dims[2];
   const size_t Pz = pad[0], Py = pad[1], Px = pad[2];
   const size_t vz = 2 * nz - 1, vy = 2 * ny - 1, nvox = nz * ny * nx;
+  const size_t nch = channel_fields(measure), nf = nch + 1;
   Sizes z;
-  z.f02_elems = std::max(4 * nz * ny * Px, vz * Px * Py);
-  z.f13_elems = std::max(4 * nz * Px * Py, vz * vy * Px);
+  z.f02_elems = std::max(nf * nz * ny * Px, vz * Px * Py);
+  z.f13_elems = std::max(nf * nz * Px * Py, vz * vy * Px);
   z.per_rot = (z.f02_elems + z.f13_elems) * sizeof(float2) + nvox * 5;
   z.shared_ws = nvox * sizeof(float2);
-  z.uv_elems = 7 * (Px / 2 + 1) * Py * Pz;
+  z.uv_elems = (2 * nch + 1) * (Px / 2 + 1) * Py * Pz;
   return z;
 }
 
@@ -445,8 +452,8 @@ cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int
 cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
   return ::resolve_pads_impl(dims, cfg, pad);
 }
-size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch) {
-  const Sizes z = ::sizes_for(dims, pad);
+size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure) {
+  const Sizes z = ::sizes_for(dims, pad, measure);
   int distinct = 1;
   if (pad[1] != pad[0]) ++distinct;
   if (pad[2] != pad[0] && pad[2] != pad[1]) ++distinct;
@@ -509,8 +516,10 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   g.vz = 2 * g.nz - 1; g.vy = 2 * g.ny - 1; g.vx = 2 * g.nx - 1;
   g.eps2 = cfg.eps * cfg.eps;
   g.nvox = (long long)g.nz * g.ny * g.nx;
+  g.nch = channel_fields(cfg.measure);
+  g.nf = g.nch + 1;
 
-  const Sizes sz = sizes_for(dims, pad);
+  const Sizes sz = sizes_for(dims, pad, cfg.measure);
   f->f02_elems = sz.f02_elems;
   f->f13_elems = sz.f13_elems;
   const size_t per_rot = sz.per_rot, shared_ws = sz.shared_ws, uv_elems = sz.uv_elems;

@@ -14,14 +14,16 @@
 //
 // Data layout (all [slow]...[fast], complex64 = float2):
 //   Bh, Mh   [r][z][y][x]                     float / uint8
-//   F0       [r][j][z][y][kx]     j < 4        x transformed
+//   F0       [r][j][z][y][kx]     j < nf       x transformed
 //   F1       [r][j][z][kx][ky]                  x, y transformed
 //   F2       [r][vz][kx][ky]                    Z = X + iY after the z inverse
 //   F3       [r][vz][vy][kx]                    after the y inverse
-//   UV       [7][kx <= Px/2][ky][kz]           fixed-volume weights (prepare)
+//   UV       [2nch+1][kx <= Px/2][ky][kz]      fixed-volume weights (prepare)
 // vz, vy, vx index the shift chi = v - (n - 1) in [-(n-1), n-1].
 //
-// Packed channel pairs: j=0 (xx, yy), j=1 (zz, xy), j=2 (xz, yz), j=3 (mask, 0).
+// Packed channel pairs (Eq. 2, squared measure): j=0 (xx, yy), j=1 (zz, xy),
+// j=2 (xz, yz), j=3 (mask, 0).  Eq. 3 (unsquared measure): j=0 (x, y),
+// j=1 (z, 0), j=2 (mask, 0).  F0/F1 hold g.nf fields per rotation.
 #pragma once
 
 #include "fft_core.cuh"
@@ -34,6 +36,8 @@ struct Geo {
   int vz, vy, vx;       // 2n - 1 shift extents
   float eps2;           // eps^2 (Eq. 1)
   long long nvox;       // nz*ny*nx
+  int nch;              // packed channel fields: 3 (Eq. 2, squared) or 2 (Eq. 3, unsquared)
+  int nf;               // fields per rotation: nch + 1 (the mask field is last)
 };
 
 // per-rotation matrix (row-major, acts on (x, y, z)), rounded to FP32 on the host

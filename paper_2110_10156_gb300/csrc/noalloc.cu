@@ -201,6 +201,8 @@ extern "C" cs_ngf_status cs_ngf_score_rotations_noalloc(
   g.vz = 2 * g.nz - 1; g.vy = 2 * g.ny - 1; g.vx = 2 * g.nx - 1;
   g.eps2 = eps * eps;
   g.nvox = (long long)g.nz * g.ny * g.nx;
+  g.nch = 3;                         // Eq. 2 (squared) measure
+  g.nf = 4;
 
   float2* UV = (float2*)(base + kOffUV);
   float2* F02 = (float2*)(base + kOffF02);

@@ -67,15 +67,20 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
   }
   const long long rows_per_field = (long long)g.nz * g.ny;
 #pragma unroll 1
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < g.nf; ++j) {
+    // Eq. 6 products (squared measure) or Eq. 3 components (unsquared); the
+    // mask field comes last
+    const int code = j == g.nch ? 3 : (g.nch == 3 ? j : 4 + j);
     float2 v[H];
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) {
       const float m = mm[n1];
-      switch (j) {
+      switch (code) {
         case 0: v[n1] = make_float2(m * vx[n1] * vx[n1], m * vy[n1] * vy[n1]); break;
         case 1: v[n1] = make_float2(m * vz[n1] * vz[n1], m * vx[n1] * vy[n1]); break;
         case 2: v[n1] = make_float2(m * vx[n1] * vz[n1], m * vy[n1] * vz[n1]); break;
+        case 4: v[n1] = make_float2(m * vx[n1], m * vy[n1]); break;
+        case 5: v[n1] = make_float2(m * vz[n1], 0.0f); break;
         default: v[n1] = make_float2(m, 0.0f); break;
       }
     }
@@ -90,7 +95,7 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
         const long long rz2 = gr / g.ny;
         const int y2 = (int)(gr - rz2 * g.ny);
         const int r2 = (int)(rz2 / g.nz), z2 = (int)(rz2 - (long long)r2 * g.nz);
-        float2* dst = F0 + ((((long long)r2 * 4 + j) * rows_per_field + (long long)z2 * g.ny + y2) * P);
+        float2* dst = F0 + ((((long long)r2 * g.nf + j) * rows_per_field + (long long)z2 * g.ny + y2) * P);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
       }
@@ -157,7 +162,7 @@ void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nro
   constexpr int W = 16, N2 = Split<P>::N2;
   const size_t smem = (size_t)W * FourStep<P>::CS * sizeof(float2);
   set_smem(k_fwd_y<P, W>, smem);
-  dim3 grid((unsigned)(nrot * 4 * g.nz), (unsigned)((g.Px + W - 1) / W));
+  dim3 grid((unsigned)(nrot * g.nf * g.nz), (unsigned)((g.Px + W - 1) / W));
   k_fwd_y<P, W><<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
 }
 
@@ -214,7 +219,7 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
   // z = N2*n1 + n2 < nz <= P/2 only for n1 < N1/2
   float2 pf[H];
   auto fetch = [&](int r, int j) {
-    const float2* src = F1 + ((long long)r * 4 + j) * g.nz * plane_stride + col_off;
+    const float2* src = F1 + ((long long)r * g.nf + j) * g.nz * plane_stride + col_off;
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) {
       const int z = N2 * n1 + n2;
@@ -227,7 +232,7 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
   // ky0..ky0+W-1 are contiguous in [kx][ky][kz]); rows past Py are zero
   {
     const int valid = min(W, g.Py - ky0) * P;
-    for (int a = 0; a < 7; ++a) {
+    for (int a = 0; a < 2 * g.nch + 1; ++a) {
       const float4* src = reinterpret_cast<const float4*>(UV + a * S7 + ((long long)kx * g.Py + ky0) * P);
       float4* dst = reinterpret_cast<float4*>(uvs + a * TILE);
       for (int q = t; q < TILE / 2; q += NT)
@@ -240,11 +245,11 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
 #pragma unroll
     for (int m = 0; m < MI; ++m) X[m] = Y[m] = make_float2(0.f, 0.f);
 #pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < g.nf; ++j) {
       float2 v[H];
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) v[n1] = pf[n1];
-      if (j < 3) fetch(r, j + 1);              // next field's loads overlap this one's work
+      if (j + 1 < g.nf) fetch(r, j + 1);       // next field's loads overlap this one's work
       else if (r + 1 < nrot) fetch(r + 1, 0);
       FS::template step1_half<-1>(v, ex + c1 * CS, n2, tw);
       __syncthreads();
@@ -258,7 +263,7 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
       __syncthreads();
       // Eq. 7-8: the weighted channel products (separated through the mirror
       // column) and the mask product, accumulated in registers
-      if (j < 3) {
+      if (j < g.nch) {
         const float2* Us = uvs + (2 * j) * TILE;
         const float2* Vs = uvs + (2 * j + 1) * TILE;
 #pragma unroll
@@ -272,7 +277,7 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
           }
         }
       } else {
-        const float2* Ms = uvs + 6 * TILE;
+        const float2* Ms = uvs + 2 * g.nch * TILE;
 #pragma unroll
         for (int m = 0; m < MI; ++m) {
           const int i = t + NT * m;
@@ -332,11 +337,11 @@ void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* t
 }
 
 // ---------------------------------------------------------------------------
-// prep_z (fixed volume, once): z-axis FFT of A's four packed fields, channel
+// prep_z (fixed volume, once): z-axis FFT of A's packed fields, channel
 // separation via the mirror column, and the weights
 //   U_j = (w_a conj(A_a) - i w_b conj(A_b)) / 2,  V_j = (w_a conj(A_a) + i w_b conj(A_b)) / 2
-// for pairs j < 3 (channels a = 2j, b = 2j+1 with Eq. 6 weights), and
-// U_3 = conj(A_mask), stored for kx <= Px/2.
+// for the channel fields j < nch (channels a, b of the pair with their Eq. 6
+// weights, or Eq. 3 weights), and conj(A_mask) last, stored for kx <= Px/2.
 // ---------------------------------------------------------------------------
 template <int P, int W>
 __global__ void __launch_bounds__(2 * W * Split<P>::N2)
@@ -359,9 +364,12 @@ k_prep_z(const float2* __restrict__ F1, float2* __restrict__ UV, const float2* _
   const bool has2 = t < NC * N1;
   const int c2 = t % NC, k1 = t / NC;
   const long long plane_stride = (long long)g.Px * g.Py;
-  const float wts[3][2] = {{1.f, 1.f}, {1.f, 2.f}, {2.f, 2.f}};
 #pragma unroll 1
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < g.nf; ++j) {
+    // Eq. 6 weights: squared (1,1), (1,2), (2,2); unsquared (Eq. 3) (1,1), (1,0)
+    float wa = 1.f, wb = 1.f;
+    if (g.nch == 3) { wa = j == 2 ? 2.f : 1.f; wb = j == 0 ? 1.f : 2.f; }
+    else { wb = j == 0 ? 1.f : 0.f; }
     const float2* src = F1 + (long long)j * g.nz * plane_stride;
     float2 v[FS::H];                      // z < nz <= P/2: upper half is zero
 #pragma unroll
@@ -389,19 +397,19 @@ k_prep_z(const float2* __restrict__ F1, float2* __restrict__ UV, const float2* _
         if (ky < g.Py) {
           const float2 h = ex[c * CS + kz];
           const long long o = ((long long)kx * g.Py + ky) * P + kz;
-          if (j < 3) {
+          if (j < g.nch) {
             const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
             // A_a = (h + hm)/2, A_b = -i (h - hm)/2
             const float2 Aa = cscale(cadd(h, hm), 0.5f);
             const float2 d = cscale(csub(h, hm), 0.5f);
             const float2 Ab = make_float2(d.y, -d.x);
-            const float2 ca = cscale(cconj(Aa), wts[j][0]);
-            const float2 cb = cscale(cconj(Ab), wts[j][1]);
+            const float2 ca = cscale(cconj(Aa), wa);
+            const float2 cb = cscale(cconj(Ab), wb);
             const float2 icb = make_float2(-cb.y, cb.x);          // i * cb
             UV[(2 * j) * S7 + o] = cscale(csub(ca, icb), 0.5f);
             UV[(2 * j + 1) * S7 + o] = cscale(cadd(ca, icb), 0.5f);
           } else {
-            UV[6 * S7 + o] = cconj(h);
+            UV[2 * g.nch * S7 + o] = cconj(h);
           }
         }
       }

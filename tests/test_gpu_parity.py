@@ -221,3 +221,28 @@ def test_graph_replay_matches_direct_launches(cs):
     d = [t.cpu().numpy() for t in g.score_rotations(dev(p.B), dev(p.MB), p.quats)]
     np.testing.assert_array_equal(c[0], d[0])
     np.testing.assert_array_equal(c[1], d[1])
+
+
+# ------------------------------------------------------------ Eq. 3 (US-NGF)
+@pytest.mark.parametrize("dims,pad", [((12, 10, 14), None), ((20, 17, 23), None), ((9, 8, 10), (400, 32, 160))])
+def test_unsquared_measure_matches_oracle(cs, dims, pad):
+    p = synth.small_pair(211 + sum(dims), dims, masks="threshold")
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, measure="unsquared")
+    for q in (IDENTITY, p.q_true, rand_quat(7)):
+        gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad, measure="unsquared")
+        check_maps(omap, gmap)
+    sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+    for r, q in enumerate(p.quats):
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad, measure="unsquared")
+        check_best_against_map(omap, sc[r], sh[r])
+
+
+def test_unsquared_measure_flips_sign_under_negation(cs):
+    p = synth.small_pair(223, (16, 14, 12))
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), measure="unsquared")
+    m1 = f.score_map(dev(p.B), dev(p.MB), IDENTITY).cpu().numpy()
+    m2 = f.score_map(dev(-p.B), dev(p.MB), IDENTITY).cpu().numpy()
+    fin = np.isfinite(m1)
+    np.testing.assert_array_equal(fin, np.isfinite(m2))
+    np.testing.assert_allclose(m2[fin], -m1[fin], rtol=0, atol=1e-6)

@@ -370,3 +370,78 @@ def test_planted_mistakes_are_caught(mutation, monkeypatch):
         monkeypatch.setattr(O, "sample_points_f32",
                             lambda R, dims: tuple(reversed(orig_s(R, dims))))
     assert not _pins_pass(), f"mutation {mutation} went unnoticed"
+
+
+# ------------------------------------------------------------ Eq. 3 (US-NGF)
+def brute_us(A, MA, B, MB, eps, gamma):
+    """Eq. 1, 3 and 5 with scalar loops only."""
+    nz, ny, nx = A.shape
+
+    def nvec(V, z, y, x):
+        def at(zz, yy, xx):
+            return V[min(max(zz, 0), nz - 1), min(max(yy, 0), ny - 1), min(max(xx, 0), nx - 1)]
+        g = ((at(z, y, x + 1) - at(z, y, x - 1)) / 2, (at(z, y + 1, x) - at(z, y - 1, x)) / 2,
+             (at(z + 1, y, x) - at(z - 1, y, x)) / 2)
+        den = math.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2 + eps ** 2)
+        return [v / den for v in g]
+
+    thr = max(1, math.ceil(gamma * min(int(MA.sum()), int(MB.sum()))))
+    out = {}
+    for chi in itertools.product(*[range(-(n - 1), n) for n in A.shape]):
+        num, N = 0.0, 0
+        for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+            zb, yb, xb = z + chi[0], y + chi[1], x + chi[2]
+            if 0 <= zb < nz and 0 <= yb < ny and 0 <= xb < nx and MA[z, y, x] and MB[zb, yb, xb]:
+                a, b = nvec(A, z, y, x), nvec(B, zb, yb, xb)
+                num += a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+                N += 1
+        out[chi] = num / N if N >= thr else -np.inf
+    return out
+
+
+def test_unsquared_direct_matches_brute_force_tiny():
+    A, MA, B, MB = rand_case(12, (3, 3, 4))
+    s, _ = O.csngf_direct(A, MA, B, MB, 0.05, 0.5, measure="unsquared")
+    for chi, v in brute_us(A, MA, B, MB, 0.05, 0.5).items():
+        idx = tuple(c + n - 1 for c, n in zip(chi, A.shape))
+        if np.isfinite(v):
+            assert s[idx] == pytest.approx(v, rel=1e-12, abs=1e-14)
+        else:
+            assert not np.isfinite(s[idx])
+
+
+def test_unsquared_fft_equals_direct():
+    A, MA, B, MB = rand_case(13, (6, 7, 5))
+    s_d, _ = O.csngf_direct(A, MA, B, MB, 1e-3, 0.5, measure="unsquared")
+    s_f, _ = O.csngf_fft(A, MA, B, MB, 1e-3, 0.5, measure="unsquared")
+    fin = np.isfinite(s_d)
+    assert np.array_equal(fin, np.isfinite(s_f))
+    np.testing.assert_allclose(s_f[fin], s_d[fin], rtol=1e-10, atol=1e-12)
+
+
+def test_unsquared_is_sign_sensitive_and_bounded():
+    A, MA, B, MB = rand_case(14, (6, 6, 6))
+    s1, _ = O.csngf_fft(A, MA, B, MB, 1e-3, 0.5, measure="unsquared")
+    s2, _ = O.csngf_fft(A, MA, -B, MB, 1e-3, 0.5, measure="unsquared")
+    fin = np.isfinite(s1)
+    np.testing.assert_allclose(s2[fin], -s1[fin], rtol=1e-12, atol=1e-14)
+    assert s1[fin].min() >= -1 - 1e-12 and s1[fin].max() <= 1 + 1e-12
+
+
+def test_unsquared_ramps_closed_form_with_rotation():
+    n = 13
+    zz, yy, xx = np.meshgrid(*[np.arange(n, dtype=float) for _ in range(3)], indexing="ij")
+    uA, uB = np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.6, 0.8])
+    a, b = 2e-5, 5e-5
+    A = a * (uA[0] * xx + uA[1] * yy + uA[2] * zz)
+    B = b * (uB[0] * xx + uB[1] * yy + uB[2] * zz)
+    MA = np.zeros((n, n, n), np.uint8)
+    MA[1:-1, 1:-1, 1:-1] = 1
+    MB = np.zeros((n, n, n), np.uint8)
+    MB[3:-3, 3:-3, 3:-3] = 1
+    q = synth.axis_angle_quaternion([0.3, 1.0, 0.2], 0.5)
+    R = O.quat_to_rotmat(q)
+    s, _ = O.score_map(A, MA, B, MB, q, eps=1e-5, measure="unsquared")
+    fin = s[np.isfinite(s)]
+    expect = (uA @ (R.T @ uB)) * math.sqrt(a * a / (a * a + 1e-10)) * math.sqrt(b * b / (b * b + 1e-10))
+    np.testing.assert_allclose(fin, expect, rtol=2e-7)
