@@ -31,8 +31,9 @@
  *     sum M_hat))).  Masks are 0/1 bytes (nonzero counts as 1).
  *   - Ties: the larger score wins; equal scores go to the smallest
  *     (chi_z, chi_y, chi_x), then to the smallest rotation index.
- *   - FFT lengths: per axis the smallest of {16, 32, 64, 128, 160, 200, 256,
- *     320, 400, 512} that is >= 2n - 1 (full linear correlation), unless set.
+ *   - FFT lengths: per axis the smallest of {16, 32, 40, 64, 80, 100, 128,
+ *     160, 200, 256, 320, 400, 512} that is >= 2n - 1 (full linear
+ *     correlation), unless set.
  *
  * Memory and streams: array arguments are DEVICE pointers owned by the
  * caller unless a function says "host".  Work is enqueued on `stream` (a
@@ -269,6 +270,49 @@ cs_ngf_status cs_ngf_server_wait(cs_ngf_server* s, int64_t job_id, double timeou
 cs_ngf_status cs_ngf_server_stats(cs_ngf_server* s, cs_ngf_server_info* info);
 /* Cancel what is left, stop the worker and free every device resource. */
 void cs_ngf_server_destroy(cs_ngf_server* s);
+
+/* ---------------------------------------------------------------------------
+ * Global rigid alignment (Section 3.2): rotations by random search around
+ * starting points, the shift of each rotation from the all-shift similarity,
+ * inside an m-level Gaussian pyramid.  Level k smooths both volumes with a
+ * Gaussian of sigma[k] voxels (truncated at 4 sigma, faces clamped), keeps
+ * every downsample[k]-th voxel (masks sampled at the same voxels), and scores
+ * its starting points plus random_rotations[k] rotations, each a uniformly
+ * chosen starting point plus U(-max_step_deg[k], max_step_deg[k]) on each
+ * Euler angle (about x, then the resulting y, then the resulting z).  The
+ * best starting_points[k+1] become the next level's starting points.
+ * Random numbers: SplitMix64 seeded with `seed`; per random rotation one
+ * uniform draw picks the starting point, then one per angle (x, y, z).  The paper's
+ * schedule (cs_ngf_search_default_config): sigma (5, 3, 2, 1.5), d (4, 2, 2,
+ * 1), u (180, 30, 10, 0), a (5000, 3000, 300, 0), p (1, 20, 3, 1), start (0,
+ * 0, 0).  Inputs are device arrays of `dims`; the call allocates its level
+ * buffers and one handle per level, and synchronises `stream`. */
+#define CS_NGF_MAX_LEVELS 8
+typedef struct {
+  int32_t levels;
+  float sigma[CS_NGF_MAX_LEVELS];
+  int32_t downsample[CS_NGF_MAX_LEVELS];
+  float max_step_deg[CS_NGF_MAX_LEVELS];
+  int32_t random_rotations[CS_NGF_MAX_LEVELS];
+  int32_t starting_points[CS_NGF_MAX_LEVELS];
+  float start_euler_deg[3];
+  uint64_t seed;
+} cs_ngf_search_config;
+
+typedef struct {
+  float score;                          /* best score at the last level */
+  float level_best[CS_NGF_MAX_LEVELS];  /* best score found at each level */
+  double euler_deg[3];                  /* best rotation (x, y', z'' Euler angles, degrees) */
+  double quat[4];                       /* the same rotation as a unit quaternion (w, x, y, z) */
+  int32_t shift[3];                     /* best shift (chi_z, chi_y, chi_x) in full-resolution voxels */
+  int64_t rotations_scored;             /* rotations scored over all levels */
+} cs_ngf_search_result;
+
+void cs_ngf_search_default_config(cs_ngf_search_config* cfg);
+cs_ngf_status cs_ngf_global_align(const float* A, const uint8_t* maskA, const float* B,
+                                  const uint8_t* maskB, const int32_t dims[3],
+                                  const cs_ngf_config* cfg, const cs_ngf_search_config* search,
+                                  void* stream, cs_ngf_search_result* out);
 
 /* Sizes and FFT lengths of a handle.  info: host. */
 cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info);

@@ -31,7 +31,10 @@ EXPORTED = (
     "cs_ngf_launch_count", "cs_ngf_score_rotations_noalloc",
     "cs_ngf_server_default_config", "cs_ngf_server_create", "cs_ngf_server_submit",
     "cs_ngf_server_cancel", "cs_ngf_server_wait", "cs_ngf_server_stats", "cs_ngf_server_destroy",
+    "cs_ngf_search_default_config", "cs_ngf_global_align",
 )
+
+MAX_LEVELS = 8
 
 STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "other")
 
@@ -66,6 +69,19 @@ class ServerInfo(ctypes.Structure):
     _fields_ = [("pending", ctypes.c_int32), ("active", ctypes.c_int32), ("slots", ctypes.c_int32),
                 ("reserved_", ctypes.c_int32), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_int64), ("memory_budget_bytes", ctypes.c_int64)]
+
+
+class SearchConfig(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("sigma", ctypes.c_float * 8),
+                ("downsample", ctypes.c_int32 * 8), ("max_step_deg", ctypes.c_float * 8),
+                ("random_rotations", ctypes.c_int32 * 8), ("starting_points", ctypes.c_int32 * 8),
+                ("start_euler_deg", ctypes.c_float * 3), ("seed", ctypes.c_uint64)]
+
+
+class SearchResult(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_float), ("level_best", ctypes.c_float * 8),
+                ("euler_deg", ctypes.c_double * 3), ("quat", ctypes.c_double * 4),
+                ("shift", ctypes.c_int32 * 3), ("rotations_scored", ctypes.c_int64)]
 
 
 _vp, _i32, _p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER
@@ -105,6 +121,11 @@ _lib.cs_ngf_server_destroy.restype = None
 for _name in ("cs_ngf_server_create", "cs_ngf_server_submit", "cs_ngf_server_cancel",
               "cs_ngf_server_wait", "cs_ngf_server_stats"):
     getattr(_lib, _name).restype = _i32
+_lib.cs_ngf_search_default_config.argtypes = [_p(SearchConfig)]
+_lib.cs_ngf_search_default_config.restype = None
+_lib.cs_ngf_global_align.argtypes = [_vp, _vp, _vp, _vp, _p(_i32), _p(Config), _p(SearchConfig), _vp,
+                                     _p(SearchResult)]
+_lib.cs_ngf_global_align.restype = _i32
 _lib.cs_ngf_launch_count.argtypes = []
 _lib.cs_ngf_launch_count.restype = ctypes.c_int64
 for _name in ("cs_ngf_update_fixed", "cs_ngf_set_profiling", "cs_ngf_stage_times",
@@ -424,6 +445,40 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def global_align(A, MA, B, MB, schedule=None, seed=0x5EED, start=(0.0, 0.0, 0.0), eps=1e-5,
+                 gamma=0.5, measure="squared", stream=None):
+    """Pyramid random search of Section 3.2 (cs_ngf_global_align) on device
+    volumes.  schedule: list of (sigma, d, u_deg, a, p) per level, p being the
+    number of starting points of that level (the first level's p is 1); None
+    = the paper's schedule.  Returns a dict with score, euler_deg, quat, shift,
+    level_best and rotations_scored."""
+    import torch
+    sc = SearchConfig()
+    _lib.cs_ngf_search_default_config(ctypes.byref(sc))
+    if schedule is not None:
+        if not 1 <= len(schedule) <= MAX_LEVELS:
+            raise ValueError("1 to 8 levels")
+        sc.levels = len(schedule)
+        for k, (sigma, d, u, a, p) in enumerate(schedule):
+            sc.sigma[k], sc.downsample[k], sc.max_step_deg[k] = float(sigma), int(d), float(u)
+            sc.random_rotations[k], sc.starting_points[k] = int(a), int(p)
+    sc.seed = int(seed)
+    for i in range(3):
+        sc.start_euler_deg[i] = float(start[i])
+    cfg = Config()
+    _lib.cs_ngf_default_config(ctypes.byref(cfg))
+    cfg.eps, cfg.gamma, cfg.measure = float(eps), float(gamma), MEASURES[measure]
+    dims = (ctypes.c_int32 * 3)(*tuple(A.shape))
+    res = SearchResult()
+    _check(_lib.cs_ngf_global_align(_dev_ptr(A, torch.float32, "A"), _dev_ptr(MA, torch.uint8, "maskA"),
+                                    _dev_ptr(B, torch.float32, "B"), _dev_ptr(MB, torch.uint8, "maskB"),
+                                    dims, ctypes.byref(cfg), ctypes.byref(sc), _stream_ptr(stream),
+                                    ctypes.byref(res)), "cs_ngf_global_align")
+    return dict(score=float(res.score), euler_deg=tuple(res.euler_deg), quat=tuple(res.quat),
+                shift=tuple(res.shift), level_best=[float(res.level_best[k]) for k in range(sc.levels)],
+                rotations_scored=int(res.rotations_scored))
 
 
 def prepare_fixed(A, MA, **kw) -> Fixed:

@@ -43,7 +43,7 @@ namespace {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                     \
   } while (0)
 
-constexpr int kPads[] = {16, 32, 64, 128, 160, 200, 256, 320, 400, 512};
+constexpr int kPads[] = {16, 32, 40, 64, 80, 100, 128, 160, 200, 256, 320, 400, 512};
 
 bool pad_supported(int p) {
   for (int v : kPads)
@@ -137,7 +137,10 @@ struct Stage {
   switch (P) {                                                                          \
     case 16: { constexpr int PP = 16; CALL; } break;                                    \
     case 32: { constexpr int PP = 32; CALL; } break;                                    \
+    case 40: { constexpr int PP = 40; CALL; } break;                                    \
     case 64: { constexpr int PP = 64; CALL; } break;                                    \
+    case 80: { constexpr int PP = 80; CALL; } break;                                    \
+    case 100: { constexpr int PP = 100; CALL; } break;                                  \
     case 128: { constexpr int PP = 128; CALL; } break;                                  \
     case 160: { constexpr int PP = 160; CALL; } break;                                  \
     case 200: { constexpr int PP = 200; CALL; } break;                                  \

@@ -185,7 +185,10 @@ template <int N>
 struct Split;   // N = N1 * N2 with N1 <= N2 (step 2 then has at most one item per thread)
 template <> struct Split<16>  { static constexpr int N1 = 4,  N2 = 4; };
 template <> struct Split<32>  { static constexpr int N1 = 4,  N2 = 8; };
+template <> struct Split<40>  { static constexpr int N1 = 4,  N2 = 10; };
 template <> struct Split<64>  { static constexpr int N1 = 8,  N2 = 8; };
+template <> struct Split<80>  { static constexpr int N1 = 8,  N2 = 10; };
+template <> struct Split<100> { static constexpr int N1 = 10, N2 = 10; };
 template <> struct Split<128> { static constexpr int N1 = 8,  N2 = 16; };
 template <> struct Split<160> { static constexpr int N1 = 8,  N2 = 20; };
 template <> struct Split<200> { static constexpr int N1 = 8,  N2 = 25; };

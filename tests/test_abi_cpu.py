@@ -69,7 +69,7 @@ def test_prepare_rejects_bad_arguments_before_touching_the_device(binding):
     cfg.gamma = 1.5
     assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None, ctypes.byref(h)) == binding.EINVAL
     cfg.gamma = 0.5
-    cfg.pad[0] = 100                      # not a supported FFT length
+    cfg.pad[0] = 96                       # not a supported FFT length
     assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None,
                                     ctypes.byref(h)) == binding.EUNSUPPORTED
     cfg.pad[0] = 16                       # < 2n - 1 for n = 9
