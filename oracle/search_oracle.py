@@ -65,13 +65,16 @@ def level_volume(V, M, sigma, d):
 
 
 def global_align(A, MA, B, MB, schedule, seed, eps=1e-5, gamma=0.5, start=(0.0, 0.0, 0.0)):
-    """schedule: list of (sigma, d, u_deg, a, p_next) per level.  Returns
-    (score, euler_deg, shift_full_res, level_best, candidates_per_level)."""
+    """schedule: list of (sigma, d, u_deg, a, p) per level, p being that
+    level's number of starting points (the paper's p_k = |Theta_k|; the first
+    level starts from `start` alone).  Level k keeps its best p_{k+1}
+    rotations for level k + 1.  Returns (score, euler_deg, shift_full_res,
+    level_best, candidates_per_level)."""
     rng = SplitMix64(seed)
     starts = [tuple(float(v) for v in start)]
     level_best, cands_log = [], []
     result = None
-    for k, (sigma, d, u, a, p_next) in enumerate(schedule):
+    for k, (sigma, d, u, a, _p) in enumerate(schedule):
         Ak, MAk = level_volume(A, MA, sigma, d)
         Bk, MBk = level_volume(B, MB, sigma, d)
         cand = list(starts)
@@ -87,7 +90,7 @@ def global_align(A, MA, B, MB, schedule, seed, eps=1e-5, gamma=0.5, start=(0.0, 
                                                          -scores[i] if np.isfinite(scores[i]) else 0.0, i))
         level_best.append(float(scores[order[0]]))
         cands_log.append((cand, scores, shifts))
-        keep = p_next if k + 1 < len(schedule) else 1
+        keep = schedule[k + 1][4] if k + 1 < len(schedule) else 1
         starts = [cand[i] for i in order[:keep]]
         b = order[0]
         result = (float(scores[b]), cand[b], tuple(int(v) * d for v in shifts[b]))
