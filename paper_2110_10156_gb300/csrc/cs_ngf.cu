@@ -167,6 +167,9 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->F02);
   cudaFree(f->F13);
   cudaFree(f->msum);
+  cudaFree(f->margA);
+  cudaFree(f->margB);
+  cudaFree(f->bounds);
   cudaFree(f->thr);
   cudaFree(f->keys);
   for (int a = 0; a < 3; ++a) {
@@ -242,11 +245,11 @@ cs_ngf_status run_transforms(cs_ngf_fixed* f, int nb, float* map, cudaStream_t s
   if (cs_ngf_status s = check_launch("fwd_x")) return s;
   { Stage sp(f, 2, st); CS_DISPATCH(g.Py, launch_fwd_y<PP>(f->F02, f->F13, f->tw[1], g, nb, st)); }
   if (cs_ngf_status s = check_launch("fwd_y")) return s;
-  { Stage sp(f, 3, st); CS_DISPATCH(g.Pz, launch_zmac<PP>(f->F13, f->UV, f->F02, f->tw[0], g, nb, st)); }
+  { Stage sp(f, 3, st); CS_DISPATCH(g.Pz, launch_zmac<PP>(f->F13, f->UV, f->F02, f->tw[0], g, nb, f->bounds, st)); }
   if (cs_ngf_status s = check_launch("zmac")) return s;
-  { Stage sp(f, 4, st); CS_DISPATCH(g.Py, launch_inv_y<PP>(f->F02, f->F13, f->tw[1], g, nb, st)); }
+  { Stage sp(f, 4, st); CS_DISPATCH(g.Py, launch_inv_y<PP>(f->F02, f->F13, f->tw[1], g, nb, f->bounds, st)); }
   if (cs_ngf_status s = check_launch("inv_y")) return s;
-  { Stage sp(f, 5, st); CS_DISPATCH(g.Px, launch_inv_x<PP>(f->F13, f->thr, f->keys, map, f->tw[2], g, nb, st)); }
+  { Stage sp(f, 5, st); CS_DISPATCH(g.Px, launch_inv_x<PP>(f->F13, f->thr, f->keys, map, f->tw[2], g, nb, f->bounds, st)); }
   if (cs_ngf_status s = check_launch("inv_x")) return s;
   return CS_NGF_OK;
 }
@@ -262,11 +265,13 @@ cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, 
 cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float* out_score,
                                int32_t* out_shift, float* map, cudaStream_t st) {
   const Geo& g = f->g;
+  const size_t nmarg = (size_t)g.nz + g.ny + g.nx;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int) * nb, st));
   CS_CUDA(cudaMemsetAsync(f->keys, 0, sizeof(unsigned long long) * nb, st));
+  CS_CUDA(cudaMemsetAsync(f->margB, 0, sizeof(int) * nmarg * nb, st));
   {
     Stage sp(f, 0, st);
-    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, rot, g, f->Bh, f->Mh, f->msum);
+    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, rot, g, f->Bh, f->Mh, f->msum, f->margB);
   }
   if (cs_ngf_status s = check_launch("resample")) return s;
   const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
@@ -275,6 +280,16 @@ cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float
     k_thresholds<<<(nb + 127) / 128, 128, 0, st>>>(f->msum, f->sumA, f->gamma, pvol, nb, f->thr);
   }
   if (cs_ngf_status s = check_launch("thresholds")) return s;
+  {
+    Stage sp(f, 7, st);
+    k_shift_bounds<<<dim3((unsigned)nb, 3u), 512, 0, st>>>(f->margA, f->margB, f->msum, f->sumA,
+                                                           f->gamma, g, f->bounds);
+  }
+  if (cs_ngf_status s = check_launch("shift bounds")) return s;
+  if (map) {
+    Stage sp(f, 7, st);
+    k_fill<<<256, 256, 0, st>>>(map, (long long)g.vz * g.vy * g.vx, -INFINITY);
+  }
   if (cs_ngf_status s = run_transforms(f, nb, map, st)) return s;
   {
     Stage sp(f, 7, st);
@@ -283,7 +298,7 @@ cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float
   return check_launch("finalize");
 }
 
-constexpr int kKernelsPerBatch = 8;   // resample, thresholds, 5 passes, finalize
+constexpr int kKernelsPerBatch = 9;   // resample, thresholds, bounds, 5 passes, finalize
 
 cs_ngf_status score_batch(cs_ngf_fixed* f, int r0, int nb, float* best_score, int32_t* best_shift,
                           float* map, cudaStream_t st) {
@@ -329,6 +344,9 @@ cs_ngf_status run_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* MA, cuda
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
   { Stage sp(f, 6, st); k_mask_sum<<<1024, 256, 0, st>>>(f->Mh, g.nvox, f->msum); }
   if (cs_ngf_status s = check_launch("mask_sum")) return s;
+  CS_CUDA(cudaMemsetAsync(f->margA, 0, sizeof(int) * ((size_t)g.nz + g.ny + g.nx), st));
+  { Stage sp(f, 6, st); k_marginals<<<1024, 256, 0, st>>>(f->Mh, g, f->margA); }
+  if (cs_ngf_status s = check_launch("marginals")) return s;
   { Stage sp(f, 6, st); CS_DISPATCH(g.Px, launch_fwd_x<PP>(f->Bh, f->Mh, f->F02, f->tw[2], g, 1, st)); }
   if (cs_ngf_status s = check_launch("fwd_x (fixed)")) return s;
   { Stage sp(f, 6, st); CS_DISPATCH(g.Py, launch_fwd_y<PP>(f->F02, f->F13, f->tw[1], g, 1, st)); }
@@ -457,13 +475,12 @@ cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int 
 }
 size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure) {
   const Sizes z = ::sizes_for(dims, pad, measure);
-  int distinct = 1;
-  if (pad[1] != pad[0]) ++distinct;
-  if (pad[2] != pad[0] && pad[2] != pad[1]) ++distinct;
   size_t tw = 0;
   for (int a = 0; a < 3; ++a) tw += (size_t)pad[a] * sizeof(float2);
+  const size_t nmarg = (size_t)dims[0] + dims[1] + dims[2];
   return z.uv_elems * sizeof(float2) + (size_t)batch * z.per_rot + z.shared_ws +
-         (size_t)batch * (sizeof(int) + sizeof(float) + sizeof(unsigned long long)) + tw + (size_t)distinct * 0;
+         (size_t)batch * (sizeof(int) + sizeof(float) + sizeof(unsigned long long) + 6 * sizeof(int)) +
+         (size_t)(batch + 1) * nmarg * sizeof(int) + tw;
 }
 }  // namespace detail
 }  // namespace csngf
@@ -548,6 +565,10 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->F02, (size_t)batch * f->f02_elems));
   CS_TRYC(dalloc(&f->F13, (size_t)batch * f->f13_elems));
   CS_TRYC(dalloc(&f->msum, (size_t)batch));
+  const size_t nmarg = (size_t)g.nz + g.ny + g.nx;
+  CS_TRYC(dalloc(&f->margA, nmarg));
+  CS_TRYC(dalloc(&f->margB, (size_t)batch * nmarg));
+  CS_TRYC(dalloc(&f->bounds, (size_t)batch * 6));
   CS_TRYC(dalloc(&f->thr, (size_t)batch));
   CS_TRYC(dalloc(&f->keys, (size_t)batch));
   f->fixed_bytes = uv_elems * sizeof(float2);
@@ -655,7 +676,7 @@ cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* ma
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
   const Geo& g = f->g;
   if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
-  k_resample<<<resample_grid(g, 1), 128, 0, st>>>(f->BM, f->rot_d, g, Bhat, Mhat, f->msum);
+  k_resample<<<resample_grid(g, 1), 128, 0, st>>>(f->BM, f->rot_d, g, Bhat, Mhat, f->msum, nullptr);
   return check_launch("resample");
 }
 

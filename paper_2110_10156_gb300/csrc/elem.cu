@@ -89,12 +89,17 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
 // Grid: (x tiles, y tiles, z tiles * rotations).
 __global__ void __launch_bounds__(128)
 k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
-           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum) {
+           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
+           int* __restrict__ marg) {
   const int ztiles = (g.nz + 3) / 4;
   const int r = blockIdx.z / ztiles, zt = blockIdx.z - r * ztiles;
-  const int x = blockIdx.x * 8 + (threadIdx.x & 7);
-  const int y = blockIdx.y * 4 + ((threadIdx.x >> 3) & 3);
-  const int z = zt * 4 + (threadIdx.x >> 5);
+  const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 3, tz = threadIdx.x >> 5;
+  const int x = blockIdx.x * 8 + tx;
+  const int y = blockIdx.y * 4 + ty;
+  const int z = zt * 4 + tz;
+  __shared__ int slab[16];                    // 4 z-planes, 4 y-rows, 8 x-columns
+  if (threadIdx.x < 16) slab[threadIdx.x] = 0;
+  __syncthreads();
   int count = 0;
   if (x < g.nx && y < g.ny && z < g.nz) {
     float val;
@@ -104,6 +109,11 @@ k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
     Bh[idx] = val;
     Mh[idx] = m;
     count = m;
+    if (m && marg) {
+      atomicAdd_block(&slab[tz], 1);
+      atomicAdd_block(&slab[4 + ty], 1);
+      atomicAdd_block(&slab[8 + tx], 1);
+    }
   }
   // block reduction of the mask count
   for (int off = 16; off > 0; off >>= 1) count += __shfl_down_sync(0xffffffffu, count, off);
@@ -115,6 +125,64 @@ k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
     const int c = warp_sums[0] + warp_sums[1] + warp_sums[2] + warp_sums[3];
     if (c) atomicAdd(&msum[r], c);
   }
+  if (marg && threadIdx.x < 16 && slab[threadIdx.x]) {
+    int* mr = marg + (long long)r * (g.nz + g.ny + g.nx);
+    const int t = threadIdx.x;
+    if (t < 4) atomicAdd(&mr[zt * 4 + t], slab[t]);
+    else if (t < 8) atomicAdd(&mr[g.nz + blockIdx.y * 4 + (t - 4)], slab[t]);
+    else atomicAdd(&mr[g.nz + g.ny + blockIdx.x * 8 + (t - 8)], slab[t]);
+  }
+}
+
+__global__ void k_marginals(const uint8_t* __restrict__ M, Geo g, int* __restrict__ marg) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.nvox;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (!M[i]) continue;
+    const int x = (int)(i % g.nx);
+    const int y = (int)((i / g.nx) % g.ny);
+    const int z = (int)(i / ((long long)g.nx * g.ny));
+    atomicAdd(&marg[z], 1);
+    atomicAdd(&marg[g.nz + y], 1);
+    atomicAdd(&marg[g.nz + g.ny + x], 1);
+  }
+}
+
+// block (rotation r, axis a); thread per shift slot v
+__global__ void k_shift_bounds(const int* __restrict__ margA, const int* __restrict__ margB,
+                               const int* __restrict__ msumB, int sumA, float gamma, Geo g,
+                               int* __restrict__ bounds) {
+  const int r = blockIdx.x, a = blockIdx.y;
+  const int n = a == 0 ? g.nz : (a == 1 ? g.ny : g.nx);
+  const int off = a == 0 ? 0 : (a == 1 ? g.nz : g.nz + g.ny);
+  const int* ma = margA + off;
+  const int* mb = margB + (long long)r * (g.nz + g.ny + g.nx) + off;
+  const int mn = min(sumA, msumB[r]);
+  double t = ceil((double)gamma * (double)mn);
+  if (t < 1.0) t = 1.0;
+  const long long thr = (long long)t;
+  __shared__ int lo_s, hi_s;
+  if (threadIdx.x == 0) { lo_s = 0x7fffffff; hi_s = -1; }
+  __syncthreads();
+  for (int v = threadIdx.x; v < 2 * n - 1; v += blockDim.x) {
+    const int c = v - (n - 1);
+    long long u = 0;
+    for (int i = max(0, -c); i < min(n, n - c); ++i) u += min(ma[i], mb[i + c]);
+    if (u >= thr) {
+      atomicMin(&lo_s, v);
+      atomicMax(&hi_s, v);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bounds[r * 6 + 2 * a] = lo_s;
+    bounds[r * 6 + 2 * a + 1] = hi_s;
+  }
+}
+
+__global__ void k_fill(float* __restrict__ p, long long n, float v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
 }
 
 __global__ void k_mask_sum(const uint8_t* __restrict__ M, long long n, int* __restrict__ out) {

@@ -26,6 +26,9 @@ struct cs_ngf_fixed {
   float2* F02 = nullptr;
   float2* F13 = nullptr;
   int* msum = nullptr;
+  int* margA = nullptr;        // slab counts of M_A per axis [nz | ny | nx]
+  int* margB = nullptr;        // the same for each rotated mask of a batch
+  int* bounds = nullptr;       // per rotation of a batch: shift slots that can be valid
   float* thr = nullptr;
   unsigned long long* keys = nullptr;
   float2* tw[3] = {nullptr, nullptr, nullptr};   // z, y, x

@@ -61,11 +61,25 @@ __device__ __forceinline__ unsigned long long make_key(float s, unsigned lin) {
 __global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict__ MB, long long n,
                           float2* __restrict__ BM);
 __global__ void k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
-                           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum);
+                           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
+                           int* __restrict__ marg);
 inline dim3 resample_grid(const Geo& g, int nrot) {
   return dim3((unsigned)((g.nx + 7) / 8), (unsigned)((g.ny + 3) / 4),
               (unsigned)(((g.nz + 3) / 4) * nrot));
 }
+
+// ----------------------------------------------------------------- shift bounds
+// Marginal mask counts per axis, [nz | ny | nx] per volume (marg in k_resample
+// fills them for each rotated mask; k_marginals for the fixed mask).  For a
+// shift chi, N(chi) <= sum_i min(a_i, b_{i + chi_axis}) over the slabs of any
+// axis, so shifts whose slab bound is below the Section 3.2 overlap threshold
+// are invalid; k_shift_bounds keeps, per rotation and axis, the range of shift
+// slots that can be valid ([lo, hi] in v = chi + n - 1; lo > hi: none).
+__global__ void k_marginals(const uint8_t* __restrict__ M, Geo g, int* __restrict__ marg);
+__global__ void k_shift_bounds(const int* __restrict__ margA, const int* __restrict__ margB,
+                               const int* __restrict__ msumB, int sumA, float gamma, Geo g,
+                               int* __restrict__ bounds);
+__global__ void k_fill(float* __restrict__ p, long long n, float v);
 
 // sum of a uint8 mask (for the fixed volume)
 __global__ void k_mask_sum(const uint8_t* __restrict__ M, long long n, int* __restrict__ out);
@@ -88,12 +102,15 @@ template <int P> void launch_fwd_x(const float* Bh, const uint8_t* Mh, float2* F
 template <int P> void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nrot,
                                    cudaStream_t st);
 template <int P> void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw,
-                                  Geo g, int nrot, cudaStream_t st);
+                                  Geo g, int nrot, const int* bounds, cudaStream_t st);
 template <int P> void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g,
                                     cudaStream_t st);
 template <int P> void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nrot,
-                                   cudaStream_t st);
+                                   const int* bounds, cudaStream_t st);
 template <int P> void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys,
-                                   float* map, const float2* tw, Geo g, int nrot, cudaStream_t st);
+                                   float* map, const float2* tw, Geo g, int nrot, const int* bounds,
+                                   cudaStream_t st);
+// bounds: per rotation {lo_z, hi_z, lo_y, hi_y, lo_x, hi_x} shift slots that can
+// be valid, or nullptr for the full range
 
 }  // namespace csngf

@@ -239,13 +239,13 @@ extern "C" cs_ngf_status cs_ngf_score_rotations_noalloc(
     RotMat m;
     for (int i = 0; i < 9; ++i) m.m[i] = (float)Rm[i];
     k_na_set_rot<<<1, 1, 0, st>>>(m, misc);                 // also zeroes the sum and key
-    k_resample<<<resample_grid(g, 1), 128, 0, st>>>(BM, &misc->rot, g, Bh, Mh, &misc->msum[1]);
+    k_resample<<<resample_grid(g, 1), 128, 0, st>>>(BM, &misc->rot, g, Bh, Mh, &misc->msum[1], nullptr);
     k_na_threshold<<<1, 1, 0, st>>>(misc, gamma, pvol);
     NA_DISPATCH(g.Px, launch_fwd_x<PP>(Bh, Mh, F02, twx, g, 1, st));
     NA_DISPATCH(g.Py, launch_fwd_y<PP>(F02, F13, twy, g, 1, st));
-    NA_DISPATCH(g.Pz, launch_zmac<PP>(F13, UV, F02, twz, g, 1, st));
-    NA_DISPATCH(g.Py, launch_inv_y<PP>(F02, F13, twy, g, 1, st));
-    NA_DISPATCH(g.Px, launch_inv_x<PP>(F13, &misc->thr, &misc->key, nullptr, twx, g, 1, st));
+    NA_DISPATCH(g.Pz, launch_zmac<PP>(F13, UV, F02, twz, g, 1, nullptr, st));
+    NA_DISPATCH(g.Py, launch_inv_y<PP>(F02, F13, twy, g, 1, nullptr, st));
+    NA_DISPATCH(g.Px, launch_inv_x<PP>(F13, &misc->thr, &misc->key, nullptr, twx, g, 1, nullptr, st));
     k_finalize<<<1, 32, 0, st>>>(&misc->key, 1, g, best_score + r, best_shift + 3 * (size_t)r);
     if (cs_ngf_status s = na_launched("rotation")) return s;
   }

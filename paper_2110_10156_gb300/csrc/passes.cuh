@@ -188,7 +188,7 @@ struct ZmacCfg {
 template <int P>
 __global__ void __launch_bounds__(ZmacCfg<P>::NT, 1)
 k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
-       const float2* __restrict__ tw, Geo g, int nrot) {
+       const float2* __restrict__ tw, Geo g, int nrot, const int* __restrict__ bounds) {
   using FS = FourStep<P>;
   constexpr int W = ZmacCfg<P>::W;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
@@ -316,10 +316,11 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
         float2 u[N2];
         FS::template step2<1>(u, ex + c2 * CS, k1);
         float2* dst = F2 + (long long)r * g.vz * plane_stride + (long long)kx2 * g.Py + ky2;
+        const int lo = bounds ? bounds[6 * r] : 0, hi = bounds ? bounds[6 * r + 1] : g.vz - 1;
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const int vz = shift_slot(k1 + N1 * k2, g.nz, P);
-          if (vz >= 0) dst[(long long)vz * plane_stride] = u[k2];
+          if (vz >= lo && vz <= hi) dst[(long long)vz * plane_stride] = u[k2];
         }
       }
     }
@@ -329,11 +330,11 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
 
 template <int P>
 void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
-                 cudaStream_t st) {
+                 const int* bounds, cudaStream_t st) {
   using C = ZmacCfg<P>;
   set_smem(k_zmac<P>, C::smem_bytes);
   dim3 grid((unsigned)((g.Py + C::W - 1) / C::W), (unsigned)(g.Px / 2 + 1));
-  k_zmac<P><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot);
+  k_zmac<P><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
 }
 
 // ---------------------------------------------------------------------------
@@ -434,13 +435,20 @@ void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g, cudaSt
 template <int P, int W>
 __global__ void __launch_bounds__(W * Split<P>::N2)
 k_inv_y(const float2* __restrict__ F2, float2* __restrict__ F3, const float2* __restrict__ tw,
-        Geo g) {
+        Geo g, const int* __restrict__ bounds) {
   using FS = FourStep<P>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
   extern __shared__ float2 ex[];
   const int t = threadIdx.x;
   const long long plane = blockIdx.x;               // r * vz + vz_i
   const int kx0 = blockIdx.y * W;
+  const int r = (int)(plane / g.vz), vzi = (int)(plane - (long long)r * g.vz);
+  int lo_y = 0, hi_y = g.vy - 1;
+  if (bounds) {                                      // planes outside the shift bound: nothing to do
+    if (vzi < bounds[6 * r] || vzi > bounds[6 * r + 1]) return;
+    lo_y = bounds[6 * r + 2];
+    hi_y = bounds[6 * r + 3];
+  }
   {
     const int row = t / N2, n2 = t - row * N2;
     const int kx = kx0 + row;
@@ -462,19 +470,20 @@ k_inv_y(const float2* __restrict__ F2, float2* __restrict__ F3, const float2* __
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
         const int vy = shift_slot(k1 + N1 * k2, g.ny, P);
-        if (vy >= 0) dst[(long long)vy * g.Px] = u[k2];
+        if (vy >= lo_y && vy <= hi_y) dst[(long long)vy * g.Px] = u[k2];
       }
     }
   }
 }
 
 template <int P>
-void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nrot, cudaStream_t st) {
+void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nrot, const int* bounds,
+                  cudaStream_t st) {
   constexpr int W = 16, N2 = Split<P>::N2;
   const size_t smem = (size_t)W * FourStep<P>::CS * sizeof(float2);
   set_smem(k_inv_y<P, W>, smem);
   dim3 grid((unsigned)(nrot * g.vz), (unsigned)((g.Px + W - 1) / W));
-  k_inv_y<P, W><<<grid, W * N2, smem, st>>>(F2, F3, tw, g);
+  k_inv_y<P, W><<<grid, W * N2, smem, st>>>(F2, F3, tw, g, bounds);
 }
 
 // ---------------------------------------------------------------------------
@@ -487,7 +496,7 @@ template <int P, int ROWS>
 __global__ void __launch_bounds__((ROWS * Split<P>::N2 + 31) / 32 * 32)
 k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
         unsigned long long* __restrict__ keys, float* __restrict__ map,
-        const float2* __restrict__ tw, Geo g) {
+        const float2* __restrict__ tw, Geo g, const int* __restrict__ bounds) {
   using FS = FourStep<P>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, NT = (ROWS * N2 + 31) / 32 * 32;
   extern __shared__ float2 ex[];
@@ -496,6 +505,12 @@ k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
   const int plane = blockIdx.y;                       // r * vz + vz_i
   const int r = plane / g.vz, vzi = plane - r * g.vz;
   const int vy0 = blockIdx.x * ROWS;
+  int lo_y = 0, hi_y = g.vy - 1, lo_x = 0, hi_x = g.vx - 1;
+  if (bounds) {                                      // outside the shift bound: nothing to do
+    const int* b = bounds + 6 * r;
+    if (vzi < b[0] || vzi > b[1] || vy0 > b[3] || vy0 + ROWS - 1 < b[2]) return;
+    lo_y = b[2]; hi_y = b[3]; lo_x = b[4]; hi_x = b[5];
+  }
   if (t < ROWS * N2) {
     const int lrow = t / N2, n2 = t - lrow * N2;
     const int vyi = vy0 + lrow;
@@ -511,7 +526,7 @@ k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
   if (t < ROWS * N1) {
     const int lr = t / N1, k1 = t - lr * N1;
     const int vyi = vy0 + lr;
-    if (vyi < g.vy) {
+    if (vyi < g.vy && vyi >= lo_y && vyi <= hi_y) {
       float2 u[N2];
       FS::template step2<1>(u, ex + lr * CS, k1);
       const float th = thr[r];
@@ -519,7 +534,7 @@ k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
         const int vxi = shift_slot(k1 + N1 * k2, g.nx, P);
-        if (vxi >= 0) {
+        if (vxi >= lo_x && vxi <= hi_x) {
           const float2 zz = u[k2];
           float s = __int_as_float(0xff800000);
           if (zz.y >= th) {
@@ -549,13 +564,13 @@ k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
 
 template <int P>
 void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys, float* map,
-                  const float2* tw, Geo g, int nrot, cudaStream_t st) {
+                  const float2* tw, Geo g, int nrot, const int* bounds, cudaStream_t st) {
   constexpr int N2 = Split<P>::N2;
   constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
   const size_t smem = (size_t)ROWS * FourStep<P>::CS * sizeof(float2);
   set_smem(k_inv_x<P, ROWS>, smem);
   dim3 grid((unsigned)((g.vy + ROWS - 1) / ROWS), (unsigned)(nrot * g.vz));
-  k_inv_x<P, ROWS><<<grid, (ROWS * N2 + 31) / 32 * 32, smem, st>>>(F3, thr, keys, map, tw, g);
+  k_inv_x<P, ROWS><<<grid, (ROWS * N2 + 31) / 32 * 32, smem, st>>>(F3, thr, keys, map, tw, g, bounds);
 }
 
 #define CSNGF_INSTANTIATE_PASSES(P)                                                              \
@@ -563,10 +578,11 @@ void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys, 
                                 cudaStream_t);                                                   \
   template void launch_fwd_y<P>(const float2*, float2*, const float2*, Geo, int, cudaStream_t);  \
   template void launch_zmac<P>(const float2*, const float2*, float2*, const float2*, Geo, int,   \
-                               cudaStream_t);                                                    \
+                               const int*, cudaStream_t);                                        \
   template void launch_prep_z<P>(const float2*, float2*, const float2*, Geo, cudaStream_t);      \
-  template void launch_inv_y<P>(const float2*, float2*, const float2*, Geo, int, cudaStream_t);  \
+  template void launch_inv_y<P>(const float2*, float2*, const float2*, Geo, int, const int*,     \
+                                cudaStream_t);                                                   \
   template void launch_inv_x<P>(const float2*, const float*, unsigned long long*, float*,        \
-                                const float2*, Geo, int, cudaStream_t);
+                                const float2*, Geo, int, const int*, cudaStream_t);
 
 }  // namespace csngf

@@ -445,3 +445,28 @@ def test_unsquared_ramps_closed_form_with_rotation():
     fin = s[np.isfinite(s)]
     expect = (uA @ (R.T @ uB)) * math.sqrt(a * a / (a * a + 1e-10)) * math.sqrt(b * b / (b * b + 1e-10))
     np.testing.assert_allclose(fin, expect, rtol=2e-7)
+
+
+# --------------------------------------------- slab bound used to prune shifts
+def slab_bound(MA, MB, axis):
+    """U(c) = sum_i min(a_i, b_{i+c}) over the slabs along one axis."""
+    others = tuple(a for a in range(3) if a != axis)
+    a = MA.sum(axis=others).astype(np.int64)
+    b = MB.sum(axis=others).astype(np.int64)
+    n = len(a)
+    return {c: sum(min(a[i], b[i + c]) for i in range(max(0, -c), min(n, n - c))) for c in range(-(n - 1), n)}
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_slab_bound_never_below_overlap(seed):
+    """N(chi) <= min over axes of the slab bound, so a shift whose bound is
+    below the overlap threshold is invalid (exact pruning of the inverse)."""
+    rng = np.random.default_rng(seed)
+    dims = (7, 8, 6)
+    MA = (rng.random(dims) < 0.5).astype(np.uint8)
+    MB = (rng.random(dims) < 0.4).astype(np.uint8)
+    _, N = O.csngf_direct(rng.random(dims), MA, rng.random(dims), MB, 1e-3, 0.5)
+    bounds = [slab_bound(MA, MB, ax) for ax in range(3)]
+    for idx in itertools.product(*[range(2 * n - 1) for n in dims]):
+        chi = [i - (n - 1) for i, n in zip(idx, dims)]
+        assert N[idx] <= min(bounds[ax][chi[ax]] for ax in range(3))
