@@ -15,8 +15,8 @@
 // Data layout (all [slow]...[fast], complex64 = float2):
 //   Bh, Mh   [r][z][y][x]                     float / uint8
 //   F0       [r][j][z][y][kx]     j < nf       x transformed
-//   F1       [r][j][z][kx][ky]                  x, y transformed
-//   F2       [r][vz][kx][ky]                    Z = X + iY after the z inverse
+//   F1       [r][j][kx][z][ky]                  x, y transformed
+//   F2       [r][kx][vz][ky]                    Z = X + iY after the z inverse
 //   F3       [r][vz][vy][kx]                    after the y inverse
 //   UV       [2nch+1][kx <= Px/2][ky][kz]      fixed-volume weights (prepare)
 // vz, vy, vx index the shift chi = v - (n - 1) in [-(n-1), n-1].

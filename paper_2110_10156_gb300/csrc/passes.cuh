@@ -150,7 +150,8 @@ k_fwd_y(const float2* __restrict__ F0, float2* __restrict__ F1, const float2* __
     if (kx < g.Px) {
       float2 u[N2];
       FS::template step2<-1>(u, ex + col * CS, k1);
-      float2* dst = F1 + (plane * g.Px + kx) * (long long)P;
+      const long long rj = plane / g.nz, z = plane - rj * g.nz;
+      float2* dst = F1 + ((rj * g.Px + kx) * g.nz + z) * (long long)P;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
     }
@@ -181,12 +182,14 @@ struct ZmacCfg {
   // (7 * W * P complex values) stays in shared memory for the whole batch
   static constexpr int W = P <= 320 ? 8 : 4;
   static constexpr int NT = 2 * W * Split<P>::N2;
+  // blocks per SM the register budget is sized for (shared memory allows it)
+  static constexpr int MIN_BLOCKS = (2 * (size_t)(7 * W * P + 2 * W * FourStep<P>::CS) * 8 <= 220 * 1024) ? 2 : 1;
   static constexpr size_t smem_bytes =
       ((size_t)7 * W * P + (size_t)2 * W * FourStep<P>::CS) * sizeof(float2);
 };
 
 template <int P>
-__global__ void __launch_bounds__(ZmacCfg<P>::NT, 1)
+__global__ void __launch_bounds__(ZmacCfg<P>::NT, ZmacCfg<P>::MIN_BLOCKS)
 k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot, const int* __restrict__ bounds) {
   using FS = FourStep<P>;
@@ -211,7 +214,7 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
   const bool ok1 = pk1 < g.Py;
   const int ky1 = c1 < W ? pk1 : (g.Py - pk1) % g.Py;
   const int kx1 = c1 < W ? kx : mkx;
-  const long long col_off = (long long)kx1 * g.Py + ky1;
+  const long long col_off = (long long)kx1 * g.nz * g.Py + ky1;   // F1 is [r][j][kx][z][ky]
   // step-2 role: column c2 (fastest), k1
   const bool has2 = t < NC * N1;
   const int c2 = t % NC, k1 = t / NC;
@@ -223,7 +226,7 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) {
       const int z = N2 * n1 + n2;
-      pf[n1] = (ok1 && z < g.nz) ? src[(long long)z * plane_stride] : make_float2(0.f, 0.f);
+      pf[n1] = (ok1 && z < g.nz) ? src[(long long)z * g.Py] : make_float2(0.f, 0.f);
     }
   };
   if (nrot > 0) fetch(0, 0);
@@ -315,12 +318,12 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
         const int kx2 = c2 < W ? kx : mkx;
         float2 u[N2];
         FS::template step2<1>(u, ex + c2 * CS, k1);
-        float2* dst = F2 + (long long)r * g.vz * plane_stride + (long long)kx2 * g.Py + ky2;
+        float2* dst = F2 + ((long long)r * g.Px + kx2) * g.vz * g.Py + ky2;   // [r][kx][vz][ky]
         const int lo = bounds ? bounds[6 * r] : 0, hi = bounds ? bounds[6 * r + 1] : g.vz - 1;
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const int vz = shift_slot(k1 + N1 * k2, g.nz, P);
-          if (vz >= lo && vz <= hi) dst[(long long)vz * plane_stride] = u[k2];
+          if (vz >= lo && vz <= hi) dst[(long long)vz * g.Py] = u[k2];
         }
       }
     }
@@ -371,12 +374,12 @@ k_prep_z(const float2* __restrict__ F1, float2* __restrict__ UV, const float2* _
     float wa = 1.f, wb = 1.f;
     if (g.nch == 3) { wa = j == 2 ? 2.f : 1.f; wb = j == 0 ? 1.f : 2.f; }
     else { wb = j == 0 ? 1.f : 0.f; }
-    const float2* src = F1 + (long long)j * g.nz * plane_stride;
+    const float2* src = F1 + (long long)j * g.nz * plane_stride;   // [j][kx][z][ky]
     float2 v[FS::H];                      // z < nz <= P/2: upper half is zero
 #pragma unroll
     for (int n1 = 0; n1 < FS::H; ++n1) {
       const int z = N2 * n1 + n2;
-      v[n1] = (ok1 && z < g.nz) ? src[(long long)z * plane_stride + (long long)kx1 * g.Py + ky1]
+      v[n1] = (ok1 && z < g.nz) ? src[((long long)kx1 * g.nz + z) * g.Py + ky1]
                                 : make_float2(0.f, 0.f);
     }
     FS::template step1_half<-1>(v, ex + c1 * CS, n2, tw);
@@ -453,7 +456,7 @@ k_inv_y(const float2* __restrict__ F2, float2* __restrict__ F3, const float2* __
     const int row = t / N2, n2 = t - row * N2;
     const int kx = kx0 + row;
     float2 v[N1];
-    const float2* src = F2 + (plane * g.Px + kx) * (long long)P;
+    const float2* src = F2 + (((long long)r * g.Px + kx) * g.vz + vzi) * (long long)P;   // [r][kx][vz][ky]
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1)
       v[n1] = (kx < g.Px) ? src[N2 * n1 + n2] : make_float2(0.f, 0.f);
