@@ -269,7 +269,7 @@ def run_ours(args):
     R = len(quats)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     A, MA, B, MB = dev(pair["A"]), dev(pair["MA"]), dev(pair["B"]), dev(pair["MB"])
-    f = cs_ngf.prepare_fixed(A, MA, batch=args.batch)
+    f = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=args.precision)
     dims, pad = f.dims, f.pad
 
     def step():
@@ -392,9 +392,10 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f32 arithmetic, bf16 channel intermediates",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "volume": list(dims), "fft": list(pad),
+            "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", "BF16 form"), "volume": list(dims), "fft": list(pad),
                        "rotations_per_gpu": R, "batch": f.batch, "masks": "thresholded foreground",
                        "l2": "inputs larger than L2: every step streams >1 TB of FFT intermediates",
                        "step": "update_fixed + score all rotations + max over rotations"},
@@ -630,6 +631,7 @@ def main():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--rotations", type=int, default=1000)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--precision", choices=("fp32", "bf16"), default="fp32")
     ap.add_argument("--ref-sample", type=int, default=16,
                     help="oracle rotations per CPU step (at most one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

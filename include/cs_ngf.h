@@ -69,12 +69,24 @@ typedef enum {
   CS_NGF_UNSQUARED = 1  /* s_US-NGF = <n_A, n_B> (Eq. 3), the USNGF method of Section 5.1 */
 } cs_ngf_measure;
 
+typedef enum {
+  CS_NGF_FP32 = 0,  /* all intermediates FP32 */
+  CS_NGF_BF16 = 1   /* NGF channel intermediates of the forward x and y passes stored as
+                       BF16 (FP32 arithmetic); the mask / overlap count path stays FP32 */
+} cs_ngf_precision;
+
 typedef struct {
-  float eps;        /* Eq. 1 regulariser; the paper uses 1e-5 */
-  float gamma;      /* minimum overlap fraction in (0, 1]; the paper uses 0.5 */
-  int32_t pad[3];   /* FFT lengths (z, y, x); 0 = automatic */
-  int32_t batch;    /* rotations per launch group; 0 = automatic (memory-sized) */
-  int32_t measure;  /* cs_ngf_measure; default CS_NGF_SQUARED */
+  float eps;         /* Eq. 1 regulariser; the paper uses 1e-5 */
+  float gamma;       /* minimum overlap fraction in (0, 1]; the paper uses 0.5 */
+  int32_t pad[3];    /* FFT lengths (z, y, x); 0 = automatic */
+  int32_t batch;     /* rotations per launch group; 0 = automatic (memory-sized);
+                        an odd value above 1 is rounded down to even, since the
+                        masks of rotations 2k and 2k+1 share one transform.
+                        Results are bit-identical for every even batch; with
+                        batch 1 each mask is transformed alone, which can change
+                        scores in the last bit */
+  int32_t measure;   /* cs_ngf_measure; default CS_NGF_SQUARED */
+  int32_t precision; /* cs_ngf_precision; default CS_NGF_FP32 */
 } cs_ngf_config;
 
 typedef struct {

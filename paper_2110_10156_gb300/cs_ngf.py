@@ -41,10 +41,12 @@ STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "othe
 
 class Config(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("gamma", ctypes.c_float),
-                ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32), ("measure", ctypes.c_int32)]
+                ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32), ("measure", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
 
 
 MEASURES = {"squared": 0, "unsquared": 1}
+PRECISIONS = {"fp32": 0, "bf16": 1}
 
 
 class Info(ctypes.Structure):
@@ -187,7 +189,7 @@ class Fixed:
     """Handle on the device-resident fixed-volume spectra (cs_ngf_prepare_fixed)."""
 
     def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None,
-                 measure="squared"):
+                 measure="squared", precision="fp32"):
         import torch
         if A.dim() != 3:
             raise ValueError("A must be [nz][ny][nx]")
@@ -203,7 +205,9 @@ class Fixed:
                 cfg.pad[i] = int(p)
         cfg.batch = int(batch)
         cfg.measure = MEASURES[measure]
+        cfg.precision = PRECISIONS[precision]
         self.measure = measure
+        self.precision = precision
         dims = (ctypes.c_int32 * 3)(*self.dims)
         h = ctypes.c_void_p()
         st = _check(_lib.cs_ngf_prepare_fixed(_dev_ptr(A, torch.float32, "A"),
@@ -384,7 +388,7 @@ class Server:
         self._R = {}
 
     def submit(self, A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, batch=0,
-               measure="squared") -> int:
+               measure="squared", precision="fp32") -> int:
         arrs = []
         for name, a, dt in (("A", A, np.float32), ("maskA", MA, np.uint8), ("B", B, np.float32),
                             ("maskB", MB, np.uint8)):
@@ -397,6 +401,7 @@ class Server:
         _lib.cs_ngf_default_config(ctypes.byref(cfg))
         cfg.eps, cfg.gamma, cfg.batch = float(eps), float(gamma), int(batch)
         cfg.measure = MEASURES[measure]
+        cfg.precision = PRECISIONS[precision]
         if pad is not None:
             for i, p in enumerate(pad):
                 cfg.pad[i] = int(p)

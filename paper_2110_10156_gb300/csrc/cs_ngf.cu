@@ -338,7 +338,8 @@ cs_ngf_status ensure_graph(cs_ngf_fixed* f) {
 
 // Section 3.1 A side: NGF channels of A times M_A, forward FFTs, weights -> f->UV
 cs_ngf_status run_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* MA, cudaStream_t st) {
-  const Geo& g = f->g;
+  Geo g = f->g;
+  g.bf16 = 0;                     // the fixed spectra are always computed in FP32
   { Stage sp(f, 6, st); k_copy_in<<<1024, 256, 0, st>>>(A, MA, g.nvox, f->Bh, f->Mh); }
   if (cs_ngf_status s = check_launch("copy_in")) return s;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
@@ -410,6 +411,8 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
   if (cfg.batch < 0) return fail(CS_NGF_EINVAL, "batch must be >= 0");
   if (cfg.measure != CS_NGF_SQUARED && cfg.measure != CS_NGF_UNSQUARED)
     return fail(CS_NGF_EINVAL, "unknown measure");
+  if (cfg.precision != CS_NGF_FP32 && cfg.precision != CS_NGF_BF16)
+    return fail(CS_NGF_EINVAL, "unknown precision");
   for (int a = 0; a < 3; ++a) {
     pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
     if (!pad_supported(pad[a]))
@@ -421,21 +424,25 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
 }
 
 struct Sizes {
-  size_t f02_elems, f13_elems, per_rot, shared_ws, uv_elems;
+  size_t f02_elems, f13_elems, fixed_f02, fixed_f13, per_rot, shared_ws, uv_elems;
 };
 
 // channel fields per measure: three packed pairs of Eq. 6 products, or two of
 // the Eq. 3 components; the mask field comes on top
 int channel_fields(int measure) { return measure == CS_NGF_UNSQUARED ? 2 : 3; }
 
-Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure) {
+Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure, int precision) {
   const size_t nz = dims[0], ny = dims[1], nx = dims[2];
   const size_t Pz = pad[0], Py = pad[1], Px = pad[2];
   const size_t vz = 2 * nz - 1, vy = 2 * ny - 1, nvox = nz * ny * nx;
   const size_t nch = channel_fields(measure), nf = nch + 1;
+  const size_t cb = precision == CS_NGF_BF16 ? 4 : 8;            // bytes per channel value
+  const size_t E0 = nz * ny * Px, E1 = nz * Px * Py;               // values per field of F0, F1
   Sizes z;
-  z.f02_elems = std::max(nf * nz * ny * Px, vz * Px * Py);
-  z.f13_elems = std::max(nf * nz * Px * Py, vz * vy * Px);
+  z.f02_elems = (std::max((nch * cb + 8) * E0, vz * Px * Py * 8) + 7) / 8;
+  z.f13_elems = (std::max((nch * cb + 8) * E1, vz * vy * Px * 8) + 7) / 8;
+  z.fixed_f02 = nf * E0;                                            // one rotation, FP32 (A side)
+  z.fixed_f13 = nf * E1;
   z.per_rot = (z.f02_elems + z.f13_elems) * sizeof(float2) + nvox * 5;
   z.shared_ws = nvox * sizeof(float2);
   z.uv_elems = (2 * nch + 1) * (Px / 2 + 1) * Py * Pz;
@@ -473,8 +480,8 @@ cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int
 cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
   return ::resolve_pads_impl(dims, cfg, pad);
 }
-size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure) {
-  const Sizes z = ::sizes_for(dims, pad, measure);
+size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision) {
+  const Sizes z = ::sizes_for(dims, pad, measure, precision);
   size_t tw = 0;
   for (int a = 0; a < 3; ++a) tw += (size_t)pad[a] * sizeof(float2);
   const size_t nmarg = (size_t)dims[0] + dims[1] + dims[2];
@@ -538,8 +545,9 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   g.nvox = (long long)g.nz * g.ny * g.nx;
   g.nch = channel_fields(cfg.measure);
   g.nf = g.nch + 1;
+  g.bf16 = cfg.precision == CS_NGF_BF16 ? 1 : 0;
 
-  const Sizes sz = sizes_for(dims, pad, cfg.measure);
+  const Sizes sz = sizes_for(dims, pad, cfg.measure, cfg.precision);
   f->f02_elems = sz.f02_elems;
   f->f13_elems = sz.f13_elems;
   const size_t per_rot = sz.per_rot, shared_ws = sz.shared_ws, uv_elems = sz.uv_elems;
@@ -550,6 +558,9 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
     const size_t budget = free_b > uv_elems * sizeof(float2) ? (free_b - uv_elems * sizeof(float2)) / 3 : 0;
     batch = (int)std::max<size_t>(1, std::min<size_t>(32, budget / per_rot));
   }
+  // the masks of rotations 2k and 2k+1 share one transform; an even batch
+  // keeps every pair inside one launch group, so results do not depend on it
+  if (batch > 1 && (batch & 1)) --batch;
   f->batch = batch;
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -562,8 +573,8 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->Bh, (size_t)batch * g.nvox));
   CS_TRYC(dalloc(&f->Mh, (size_t)batch * g.nvox));
   CS_TRYC(dalloc(&f->BM, (size_t)g.nvox));
-  CS_TRYC(dalloc(&f->F02, (size_t)batch * f->f02_elems));
-  CS_TRYC(dalloc(&f->F13, (size_t)batch * f->f13_elems));
+  CS_TRYC(dalloc(&f->F02, std::max((size_t)batch * f->f02_elems, sz.fixed_f02)));
+  CS_TRYC(dalloc(&f->F13, std::max((size_t)batch * f->f13_elems, sz.fixed_f13)));
   CS_TRYC(dalloc(&f->msum, (size_t)batch));
   const size_t nmarg = (size_t)g.nz + g.ny + g.nx;
   CS_TRYC(dalloc(&f->margA, nmarg));

@@ -60,6 +60,19 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// asynchronous global -> shared copies (cp.async, L1-allocating); the copies a
+// thread issued are visible to that thread after cp_async_wait_all()
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // a * (S i)
 template <int S>
@@ -208,14 +221,20 @@ struct FourStep {
   static constexpr int CS = (CS0 % 2 == 0) ? CS0 + 1 : CS0;
   static_assert(CS >= N, "sequence stride must hold N natural-order values");
 
+  // twiddle table read: shared memory (TS) or the read-only global path
+  template <bool TS>
+  __device__ __forceinline__ static float2 twl(const float2* p) {
+    if constexpr (TS) return *p; else return __ldg(p);
+  }
+
   // v holds x[N2*n1 + n2] for n1 = 0..N1-1; writes twiddled N1-point outputs
-  template <int S>
+  template <int S, bool TS = false>
   __device__ __forceinline__ static void step1(float2 (&v)[N1], float2* ex_seq, int n2,
                                                const float2* __restrict__ twN) {
     Dft<N1, S>::run(v);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
-      float2 w = __ldg(&twN[n2 * k1]);
+      float2 w = twl<TS>(&twN[n2 * k1]);
       if (S > 0) w.y = -w.y;
       ex_seq[n2 * RS + k1] = (k1 == 0) ? v[k1] : cmul(v[k1], w);
     }
@@ -225,7 +244,7 @@ struct FourStep {
   // of data zero-padded from length <= N/2): the N1-point DFT splits into two
   // N1/2-point DFTs, X[2m] = DFT(x)[m], X[2m+1] = DFT(x * W_N1^n)[m].
   static constexpr int H = N1 / 2;
-  template <int S>
+  template <int S, bool TS = false>
   __device__ __forceinline__ static void step1_half(float2 (&v)[H], float2* ex_seq, int n2,
                                                     const float2* __restrict__ twN) {
     static_assert(N1 % 2 == 0, "half-zero step needs an even N1");
@@ -240,7 +259,7 @@ struct FourStep {
 #pragma unroll
     for (int m = 0; m < H; ++m) {
       const int ke = 2 * m, ko = 2 * m + 1;
-      float2 we = __ldg(&twN[n2 * ke]), wo = __ldg(&twN[n2 * ko]);
+      float2 we = twl<TS>(&twN[n2 * ke]), wo = twl<TS>(&twN[n2 * ko]);
       if (S > 0) { we.y = -we.y; wo.y = -wo.y; }
       ex_seq[n2 * RS + ke] = (m == 0) ? e[m] : cmul(e[m], we);
       ex_seq[n2 * RS + ko] = cmul(o[m], wo);

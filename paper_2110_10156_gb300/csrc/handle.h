@@ -73,7 +73,7 @@ cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int
 // validate dims / cfg and return the FFT lengths; EINVAL / EUNSUPPORTED on error
 cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]);
 // device bytes a handle of these dims, FFT lengths and batch allocates
-size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure);
+size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision);
 
 }  // namespace detail
 }  // namespace csngf

@@ -26,6 +26,8 @@
 // j=1 (z, 0), j=2 (mask, 0).  F0/F1 hold g.nf fields per rotation.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "fft_core.cuh"
 
 namespace csngf {
@@ -38,6 +40,34 @@ struct Geo {
   long long nvox;       // nz*ny*nx
   int nch;              // packed channel fields: 3 (Eq. 2, squared) or 2 (Eq. 3, unsquared)
   int nf;               // fields per rotation: nch + 1 (the mask field is last)
+  int bf16;             // channel fields of F0 / F1 stored as BF16 pairs (reduced-precision form)
+};
+
+// Storage of the packed fields of F0 / F1 for a batch of rotations: the
+// channel fields j < nch hold FP32 complex values, or BF16 pairs in the
+// reduced-precision form; the mask field j = nch is always FP32 complex, so
+// the overlap count N(chi) keeps FP32 accuracy.  E = complex values per field.
+template <bool BF>
+struct Fields {
+  static constexpr int CB = BF ? 4 : 8;   // bytes per channel-field value
+  __host__ __device__ static long long rot_bytes(const Geo& g, long long E) {
+    return (long long)g.nch * E * CB + E * 8;
+  }
+  __device__ __forceinline__ static char* field(void* base, const Geo& g, long long E, int r, int j) {
+    return (char*)base + (long long)r * rot_bytes(g, E) + (long long)j * E * CB;
+  }
+  __device__ __forceinline__ static const char* field(const void* base, const Geo& g, long long E,
+                                                      int r, int j) {
+    return (const char*)base + (long long)r * rot_bytes(g, E) + (long long)j * E * CB;
+  }
+  __device__ __forceinline__ static void put(char* f, long long i, float2 v, bool mask) {
+    if (BF && !mask) reinterpret_cast<__nv_bfloat162*>(f)[i] = __float22bfloat162_rn(v);
+    else reinterpret_cast<float2*>(f)[i] = v;
+  }
+  __device__ __forceinline__ static float2 get(const char* f, long long i, bool mask) {
+    if (BF && !mask) return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(f)[i]);
+    return reinterpret_cast<const float2*>(f)[i];
+  }
 };
 
 // per-rotation matrix (row-major, acts on (x, y, z)), rounded to FP32 on the host
@@ -97,11 +127,12 @@ __global__ void k_copy_in(const float* __restrict__ A, const uint8_t* __restrict
                           long long n, float* __restrict__ Bh, uint8_t* __restrict__ Mh);
 
 // ----------------------------------------------------------------- FFT passes
-template <int P> void launch_fwd_x(const float* Bh, const uint8_t* Mh, float2* F0, const float2* tw,
+// F0 / F1 are laid out by Fields<g.bf16> (FP32 everywhere when g.bf16 == 0)
+template <int P> void launch_fwd_x(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw,
                                    Geo g, int nrot, cudaStream_t st);
-template <int P> void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nrot,
+template <int P> void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot,
                                    cudaStream_t st);
-template <int P> void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw,
+template <int P> void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw,
                                   Geo g, int nrot, const int* bounds, cudaStream_t st);
 template <int P> void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g,
                                     cudaStream_t st);

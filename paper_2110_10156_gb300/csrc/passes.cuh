@@ -24,9 +24,9 @@ static void set_smem(K kern, size_t bytes) {
 // complex fields, and the x-axis FFT of every row (zero padded to Px).
 // Block: ROWS rows of one slab; thread (row, n2) gathers x = N2*n1 + n2.
 // ---------------------------------------------------------------------------
-template <int P, int ROWS>
+template <int P, int ROWS, bool BF>
 __global__ void __launch_bounds__(ROWS * Split<P>::N2, 2)
-k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __restrict__ F0,
+k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __restrict__ F0,
         const float2* __restrict__ tw, Geo g, long long nrows) {
   using FS = FourStep<P>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
@@ -66,8 +66,16 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
     }
   }
   const long long rows_per_field = (long long)g.nz * g.ny;
+  const int nrot = (int)(nrows / rows_per_field);
+  // Masks are paired across consecutive rotations: the even rotation's mask
+  // field carries (M_r, M_{r+1}); an odd rotation has no mask field of its own.
+  const bool odd_block = ((blockIdx.x * (long long)ROWS) / rows_per_field & 1) &&
+                         (blockIdx.x * (long long)ROWS) / rows_per_field ==
+                             (min(blockIdx.x * (long long)ROWS + ROWS, nrows) - 1) / rows_per_field;
+  const bool has_partner = !(r & 1) && r + 1 < nrot;
 #pragma unroll 1
   for (int j = 0; j < g.nf; ++j) {
+    if (j == g.nch && odd_block) break;          // uniform over the block
     // Eq. 6 products (squared measure) or Eq. 3 components (unsquared); the
     // mask field comes last
     const int code = j == g.nch ? 3 : (g.nch == 3 ? j : 4 + j);
@@ -81,7 +89,13 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
         case 2: v[n1] = make_float2(m * vx[n1] * vz[n1], m * vy[n1] * vz[n1]); break;
         case 4: v[n1] = make_float2(m * vx[n1], m * vy[n1]); break;
         case 5: v[n1] = make_float2(m * vz[n1], 0.0f); break;
-        default: v[n1] = make_float2(m, 0.0f); break;
+        default: {
+          const int x = N2 * n1 + n2;
+          float m2 = 0.0f;
+          if (has_partner && row_ok && x < g.nx) m2 = M[g.nvox + base + x] ? 1.0f : 0.0f;
+          v[n1] = (r & 1) ? make_float2(0.0f, 0.0f) : make_float2(m, m2);
+          break;
+        }
       }
     }
     FS::template step1_half<-1>(v, ex + lrow * CS, n2, tw);
@@ -89,15 +103,22 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
     if (t < ROWS * N1) {
       const int lr = t / N1, k1 = t - lr * N1;
       const long long gr = (long long)blockIdx.x * ROWS + lr;
-      if (gr < nrows) {
+      const bool skip_row = j == g.nch && ((gr / rows_per_field) & 1);   // odd rotation: no mask field
+      if (gr < nrows && !skip_row) {
         float2 u[N2];
         FS::template step2<-1>(u, ex + lr * CS, k1);
         const long long rz2 = gr / g.ny;
         const int y2 = (int)(gr - rz2 * g.ny);
         const int r2 = (int)(rz2 / g.nz), z2 = (int)(rz2 - (long long)r2 * g.nz);
-        float2* dst = F0 + ((((long long)r2 * g.nf + j) * rows_per_field + (long long)z2 * g.ny + y2) * P);
+        char* fld = Fields<BF>::field(F0, g, rows_per_field * P, r2, j);
+        const long long row = ((long long)z2 * g.ny + y2) * P;
+        if (j == g.nch) {
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
+          for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(fld, row + k1 + N1 * k2, u[k2], true);
+        } else {
+#pragma unroll
+          for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(fld, row + k1 + N1 * k2, u[k2], false);
+        }
       }
     }
     __syncthreads();
@@ -105,15 +126,20 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, float2* __
 }
 
 template <int P>
-void launch_fwd_x(const float* Bh, const uint8_t* Mh, float2* F0, const float2* tw, Geo g, int nrot,
+void launch_fwd_x(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw, Geo g, int nrot,
                   cudaStream_t st) {
   constexpr int N2 = Split<P>::N2;
   constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
   const long long nrows = (long long)nrot * g.nz * g.ny;
   const size_t smem = (size_t)ROWS * FourStep<P>::CS * sizeof(float2);
-  set_smem(k_fwd_x<P, ROWS>, smem);
   const unsigned blocks = (unsigned)((nrows + ROWS - 1) / ROWS);
-  k_fwd_x<P, ROWS><<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
+  if (g.bf16) {
+    set_smem(k_fwd_x<P, ROWS, true>, smem);
+    k_fwd_x<P, ROWS, true><<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
+  } else {
+    set_smem(k_fwd_x<P, ROWS, false>, smem);
+    k_fwd_x<P, ROWS, false><<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -121,25 +147,41 @@ void launch_fwd_x(const float* Bh, const uint8_t* Mh, float2* F0, const float2* 
 // is transposed so that ky is contiguous for the z pass.
 // Block: W consecutive kx of one (r, j, z) plane.
 // ---------------------------------------------------------------------------
-template <int P, int W>
+template <int P, int W, bool BF>
 __global__ void __launch_bounds__(W * Split<P>::N2)
-k_fwd_y(const float2* __restrict__ F0, float2* __restrict__ F1, const float2* __restrict__ tw,
+k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __restrict__ tw,
         Geo g) {
   using FS = FourStep<P>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
   extern __shared__ float2 ex[];
   const int t = threadIdx.x;
-  const long long plane = blockIdx.x;
+  const long long plane = blockIdx.x;                // ((r * nf) + j) * nz + z
+  const long long rj = plane / g.nz;
+  const int z = (int)(plane - rj * g.nz);
+  const int r = (int)(rj / g.nf), j = (int)(rj - (long long)r * g.nf);
+  const bool is_mask = j == g.nch;
+  if (is_mask && (r & 1)) return;                    // paired into the even rotation's mask field
   const int kx0 = blockIdx.y * W;
   {
     const int col = t % W, n2 = t / W;
     const int kx = kx0 + col;
-    const float2* src = F0 + plane * (long long)g.ny * g.Px;
+    const char* src = Fields<BF>::field(F0, g, (long long)g.nz * g.ny * g.Px, r, j);
+    const long long zoff = (long long)z * g.ny * g.Px;
     float2 v[FS::H];                      // y < ny <= P/2: upper half is zero
+    if (is_mask) {
 #pragma unroll
-    for (int n1 = 0; n1 < FS::H; ++n1) {
-      const int y = N2 * n1 + n2;
-      v[n1] = (y < g.ny && kx < g.Px) ? src[(long long)y * g.Px + kx] : make_float2(0.f, 0.f);
+      for (int n1 = 0; n1 < FS::H; ++n1) {
+        const int y = N2 * n1 + n2;
+        v[n1] = (y < g.ny && kx < g.Px) ? Fields<BF>::get(src, zoff + (long long)y * g.Px + kx, true)
+                                        : make_float2(0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < FS::H; ++n1) {
+        const int y = N2 * n1 + n2;
+        v[n1] = (y < g.ny && kx < g.Px) ? Fields<BF>::get(src, zoff + (long long)y * g.Px + kx, false)
+                                        : make_float2(0.f, 0.f);
+      }
     }
     FS::template step1_half<-1>(v, ex + col * CS, n2, tw);
   }
@@ -150,21 +192,31 @@ k_fwd_y(const float2* __restrict__ F0, float2* __restrict__ F1, const float2* __
     if (kx < g.Px) {
       float2 u[N2];
       FS::template step2<-1>(u, ex + col * CS, k1);
-      const long long rj = plane / g.nz, z = plane - rj * g.nz;
-      float2* dst = F1 + ((rj * g.Px + kx) * g.nz + z) * (long long)P;
+      char* dst = Fields<BF>::field(F1, g, (long long)g.nz * g.Px * P, r, j);
+      const long long row = ((long long)kx * g.nz + z) * P;       // [kx][z][ky]
+      if (is_mask) {
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) dst[k1 + N1 * k2] = u[k2];
+        for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(dst, row + k1 + N1 * k2, u[k2], true);
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(dst, row + k1 + N1 * k2, u[k2], false);
+      }
     }
   }
 }
 
 template <int P>
-void launch_fwd_y(const float2* F0, float2* F1, const float2* tw, Geo g, int nrot, cudaStream_t st) {
+void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, cudaStream_t st) {
   constexpr int W = 16, N2 = Split<P>::N2;
   const size_t smem = (size_t)W * FourStep<P>::CS * sizeof(float2);
-  set_smem(k_fwd_y<P, W>, smem);
   dim3 grid((unsigned)(nrot * g.nf * g.nz), (unsigned)((g.Px + W - 1) / W));
-  k_fwd_y<P, W><<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
+  if (g.bf16) {
+    set_smem(k_fwd_y<P, W, true>, smem);
+    k_fwd_y<P, W, true><<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
+  } else {
+    set_smem(k_fwd_y<P, W, false>, smem);
+    k_fwd_y<P, W, false><<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -182,15 +234,26 @@ struct ZmacCfg {
   // (7 * W * P complex values) stays in shared memory for the whole batch
   static constexpr int W = P <= 320 ? 8 : 4;
   static constexpr int NT = 2 * W * Split<P>::N2;
-  // blocks per SM the register budget is sized for (shared memory allows it)
-  static constexpr int MIN_BLOCKS = (2 * (size_t)(7 * W * P + 2 * W * FourStep<P>::CS) * 8 <= 220 * 1024) ? 2 : 1;
+  // shared memory: fixed-spectra tile [7][W][P], transform exchange [2W][CS],
+  // the mask product of the odd rotation of a pair [W][P], the next field's
+  // inputs [N1/2][NT] and the twiddle table [P]
   static constexpr size_t smem_bytes =
-      ((size_t)7 * W * P + (size_t)2 * W * FourStep<P>::CS) * sizeof(float2);
+      ((size_t)8 * W * P + (size_t)2 * W * FourStep<P>::CS + (size_t)(Split<P>::N1 / 2) * NT + P) *
+      sizeof(float2);
+  // Registers per thread when B blocks share an SM: each of the SM's four
+  // sub-partitions holds 16384 registers and the warps placed on it, at most
+  // ceil(B * warps / 4) of them (allocation in multiples of 8 per thread).
+  static constexpr int regs_for(int B) {
+    return (16384 / (32 * ((B * ((NT + 31) / 32) + 3) / 4))) / 8 * 8;
+  }
+  // two blocks per SM where shared memory allows it and each thread still
+  // keeps at least 128 registers
+  static constexpr int MIN_BLOCKS = (2 * smem_bytes <= 220 * 1024 && regs_for(2) >= 128) ? 2 : 1;
 };
 
-template <int P>
+template <int P, bool BF>
 __global__ void __launch_bounds__(ZmacCfg<P>::NT, ZmacCfg<P>::MIN_BLOCKS)
-k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
+k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot, const int* __restrict__ bounds) {
   using FS = FourStep<P>;
   constexpr int W = ZmacCfg<P>::W;
@@ -200,6 +263,10 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
   extern __shared__ float2 smem[];
   float2* uvs = smem;                         // [7][W][P] fixed-spectra weights
   float2* ex = smem + 7 * TILE;               // [NC][CS] transform exchange
+  float2* ycarry = ex + NC * CS;              // [W][P] Y of the odd rotation of a pair;
+                                              // each thread reads back only its own slots
+  float2* stage = ycarry + TILE;              // [H][NT] next field's inputs (own slots)
+  float2* tws = stage + H * NT;               // [P] twiddles
   const int t = threadIdx.x;
   const int kx = blockIdx.y, ky0 = blockIdx.x * W;
   const int mkx = (g.Px - kx) % g.Px;
@@ -219,18 +286,49 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
   const bool has2 = t < NC * N1;
   const int c2 = t % NC, k1 = t / NC;
 
-  // z = N2*n1 + n2 < nz <= P/2 only for n1 < N1/2
-  float2 pf[H];
-  auto fetch = [&](int r, int j) {
-    const float2* src = F1 + ((long long)r * g.nf + j) * g.nz * plane_stride + col_off;
+  // z = N2*n1 + n2 < nz <= P/2 only for n1 < N1/2.  The next field's inputs
+  // are copied asynchronously into this thread's own stage slots (cp.async):
+  // no registers are held while the current field is transformed.  Slots
+  // outside the volume are zero once and never copied to.
 #pragma unroll
-    for (int n1 = 0; n1 < H; ++n1) {
-      const int z = N2 * n1 + n2;
-      pf[n1] = (ok1 && z < g.nz) ? src[(long long)z * g.Py] : make_float2(0.f, 0.f);
+  for (int n1 = 0; n1 < H; ++n1) {
+    const int z = N2 * n1 + n2;
+    if (!(ok1 && z < g.nz)) stage[n1 * NT + t] = make_float2(0.f, 0.f);
+  }
+  auto fetch = [&](int r, int j) {
+    const char* src = Fields<BF>::field(F1, g, g.nz * plane_stride, r, j);
+    if (!BF || j == g.nch) {
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) {
+        const int z = N2 * n1 + n2;
+        if (ok1 && z < g.nz)
+          cp_async8(stage + n1 * NT + t, src + (col_off + (long long)z * g.Py) * 8);
+      }
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) {
+        const int z = N2 * n1 + n2;
+        if (ok1 && z < g.nz)
+          cp_async4(stage + n1 * NT + t, src + (col_off + (long long)z * g.Py) * 4);
+      }
+    }
+    cp_async_commit();
+  };
+  // this thread's staged inputs of field j (after its copies have landed)
+  auto take = [&](float2 (&v)[H], int j) {
+    cp_async_wait_all();
+    if (!BF || j == g.nch) {
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) v[n1] = stage[n1 * NT + t];
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1)
+        v[n1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(stage + n1 * NT + t));
     }
   };
   if (nrot > 0) fetch(0, 0);
 
+  for (int q = t; q < P; q += NT) tws[q] = __ldg(&tw[q]);
   // the block's fixed-spectra tile: 7 contiguous runs of W*P values (rows
   // ky0..ky0+W-1 are contiguous in [kx][ky][kz]); rows past Py are zero
   {
@@ -242,20 +340,22 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
         dst[q] = (2 * q < valid) ? __ldg(&src[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  __syncthreads();                            // twiddles and tile visible to all
 
   for (int r = 0; r < nrot; ++r) {
     float2 X[MI], Y[MI];
 #pragma unroll
     for (int m = 0; m < MI; ++m) X[m] = Y[m] = make_float2(0.f, 0.f);
+    const int nfr = (r & 1) ? g.nch : g.nf;   // an odd rotation's mask came with its partner
 #pragma unroll 1
-    for (int j = 0; j < g.nf; ++j) {
+    for (int j = 0; j < nfr; ++j) {
       float2 v[H];
-#pragma unroll
-      for (int n1 = 0; n1 < H; ++n1) v[n1] = pf[n1];
-      if (j + 1 < g.nf) fetch(r, j + 1);       // next field's loads overlap this one's work
+      take(v, j);
+      FS::template step1_half<-1, true>(v, ex + c1 * CS, n2, tws);
+      __syncthreads();                         // (also orders this thread's stage reads
+                                               //  before the next copies into its slots)
+      if (j + 1 < nfr) fetch(r, j + 1);        // next field's copies overlap this one's work
       else if (r + 1 < nrot) fetch(r + 1, 0);
-      FS::template step1_half<-1>(v, ex + c1 * CS, n2, tw);
-      __syncthreads();
       float2 u[N2];
       if (has2) FS::template step2<-1>(u, ex + c2 * CS, k1);
       __syncthreads();
@@ -280,17 +380,30 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
           }
         }
       } else {
+        // the mask pair (M_r, M_{r+1}): M_r = (h + hm)/2, M_{r+1} = -i (h - hm)/2
         const float2* Ms = uvs + 2 * g.nch * TILE;
 #pragma unroll
         for (int m = 0; m < MI; ++m) {
           const int i = t + NT * m;
           if (i < TILE) {
             const int c = i / P, kz = i - c * P;
-            Y[m] = cmul(Ms[i], ex[c * CS + kz]);
+            const float2 h = ex[c * CS + kz];
+            const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
+            const float2 U = Ms[i];
+            Y[m] = cmul(U, cscale(cadd(h, hm), 0.5f));
+            const float2 d = cscale(csub(h, hm), 0.5f);
+            ycarry[i] = cmul(U, make_float2(d.y, -d.x));
           }
         }
       }
       __syncthreads();
+    }
+    if (r & 1) {
+#pragma unroll
+      for (int m = 0; m < MI; ++m) {
+        const int i = t + NT * m;
+        if (i < TILE) Y[m] = ycarry[i];
+      }
     }
     // Z = X + iY at k, conj(X) + i conj(Y) at -k
 #pragma unroll
@@ -308,7 +421,7 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
 #pragma unroll
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = ex[c1 * CS + N2 * n1 + n2];
       __syncthreads();
-      FS::template step1<1>(v, ex + c1 * CS, n2, tw);
+      FS::template step1<1, true>(v, ex + c1 * CS, n2, tws);
     }
     __syncthreads();
     if (has2 && !(c2 >= W && self_mirror)) {
@@ -332,12 +445,17 @@ k_zmac(const float2* __restrict__ F1, const float2* __restrict__ UV, float2* __r
 }
 
 template <int P>
-void launch_zmac(const float2* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
+void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
                  const int* bounds, cudaStream_t st) {
   using C = ZmacCfg<P>;
-  set_smem(k_zmac<P>, C::smem_bytes);
   dim3 grid((unsigned)((g.Py + C::W - 1) / C::W), (unsigned)(g.Px / 2 + 1));
-  k_zmac<P><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
+  if (g.bf16) {
+    set_smem(k_zmac<P, true>, C::smem_bytes);
+    k_zmac<P, true><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
+  } else {
+    set_smem(k_zmac<P, false>, C::smem_bytes);
+    k_zmac<P, false><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -577,10 +695,10 @@ void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys, 
 }
 
 #define CSNGF_INSTANTIATE_PASSES(P)                                                              \
-  template void launch_fwd_x<P>(const float*, const uint8_t*, float2*, const float2*, Geo, int,  \
+  template void launch_fwd_x<P>(const float*, const uint8_t*, void*, const float2*, Geo, int,    \
                                 cudaStream_t);                                                   \
-  template void launch_fwd_y<P>(const float2*, float2*, const float2*, Geo, int, cudaStream_t);  \
-  template void launch_zmac<P>(const float2*, const float2*, float2*, const float2*, Geo, int,   \
+  template void launch_fwd_y<P>(const void*, void*, const float2*, Geo, int, cudaStream_t);      \
+  template void launch_zmac<P>(const void*, const float2*, float2*, const float2*, Geo, int,      \
                                const int*, cudaStream_t);                                        \
   template void launch_prep_z<P>(const float2*, float2*, const float2*, Geo, cudaStream_t);      \
   template void launch_inv_y<P>(const float2*, float2*, const float2*, Geo, int, const int*,     \

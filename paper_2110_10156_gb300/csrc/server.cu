@@ -49,6 +49,7 @@ struct Slot {                     // device resources of one volume shape
   float eps, gamma;
   int batch;
   int measure;
+  int precision;
   cs_ngf_fixed* f = nullptr;
   float* dA = nullptr;
   uint8_t* dMA = nullptr;
@@ -113,15 +114,17 @@ struct cs_ngf_server {
 
 namespace {
 
-size_t slot_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int cap) {
+size_t slot_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision,
+                  int cap) {
   const size_t nvox = (size_t)dims[0] * dims[1] * dims[2];
-  return csngf::detail::handle_bytes(dims, pad, batch, measure) + nvox * 10 + (size_t)cap * 16;
+  return csngf::detail::handle_bytes(dims, pad, batch, measure, precision) + nvox * 10 + (size_t)cap * 16;
 }
 
 bool same_shape(const Slot& s, const Job& j) {
   return std::memcmp(s.dims, j.dims, sizeof(s.dims)) == 0 &&
          std::memcmp(s.pad, j.pad, sizeof(s.pad)) == 0 && s.eps == j.cfg.eps &&
-         s.gamma == j.cfg.gamma && s.batch == j.cfg.batch && s.measure == j.cfg.measure;
+         s.gamma == j.cfg.gamma && s.batch == j.cfg.batch && s.measure == j.cfg.measure &&
+         s.precision == j.cfg.precision;
 }
 
 void free_slot(Slot* s) {
@@ -239,6 +242,7 @@ Slot* find_slot(cs_ngf_server* sv, Job* j, bool* fresh) {
   s->gamma = j->cfg.gamma;
   s->batch = j->cfg.batch;
   s->measure = j->cfg.measure;
+  s->precision = j->cfg.precision;
   s->bytes = need;
   sv->bytes_in_use += need;
   sv->slots.push_back(std::move(s));
@@ -440,7 +444,7 @@ cs_ngf_status cs_ngf_server_submit(cs_ngf_server* sv, const float* A, const uint
   if (j->cfg.batch == 0) j->cfg.batch = sv->cfg.batch > 0 ? sv->cfg.batch : 16;
   std::memcpy(j->dims, dims, sizeof(j->dims));
   j->R = R;
-  j->bytes = slot_bytes(dims, j->pad, j->cfg.batch, j->cfg.measure, R);
+  j->bytes = slot_bytes(dims, j->pad, j->cfg.batch, j->cfg.measure, j->cfg.precision, R);
   if (j->bytes > (size_t)sv->cfg.memory_budget_bytes)
     return fail(CS_NGF_ENOMEM, "job needs " + std::to_string(j->bytes) + " device bytes, budget is " +
                                    std::to_string(sv->cfg.memory_budget_bytes));

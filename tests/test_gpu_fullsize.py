@@ -32,9 +32,19 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_150_cubed_1000_rotations(cs, pair150):
+@pytest.fixture(scope="module")
+def oracle150(pair150):
+    """The oracle's full maps (FFT form at 320^3) for q_true and two sampled rotations."""
     p = pair150
-    f = cs.prepare_fixed(dev(p.A), dev(p.MA))
+    rng = np.random.default_rng(99)
+    sample = [p.true_index] + [int(i) for i in rng.choice(len(p.quats), 2, replace=False)]
+    return {r: O.score_map(p.A, p.MA, p.B, p.MB, p.quats[r], pad=(320, 320, 320))[0] for r in sample}
+
+
+@pytest.mark.parametrize("precision,tau", [("fp32", 1e-4), ("bf16", 1e-2)])
+def test_150_cubed_1000_rotations(cs, pair150, oracle150, precision, tau):
+    p = pair150
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), precision=precision)
     assert f.pad == (320, 320, 320)
     assert f.sum_mask_a == int(p.MA.sum())
     sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
@@ -51,9 +61,6 @@ def test_150_cubed_1000_rotations(cs, pair150):
     score, ri, chi = f.align(dev(p.B), dev(p.MB), p.quats)
     assert ri == p.true_index and chi == p.t_zyx
     # sampled rotations against the oracle's full map (FFT form at 320^3)
-    rng = np.random.default_rng(99)
-    sample = [p.true_index] + [int(i) for i in rng.choice(R, 2, replace=False)]
-    for r in sample:
-        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, p.quats[r], pad=(320, 320, 320))
-        check_best_against_map(omap, sc[r], sh[r])
+    for r, omap in oracle150.items():
+        check_best_against_map(omap, sc[r], sh[r], tau=tau)
     f.release()

@@ -103,6 +103,8 @@ def test_batches_do_not_change_results(cs):
     quats = np.concatenate([p.quats, synth.random_quaternions(np.random.default_rng(4), 6)])
     f1 = cs.prepare_fixed(dev(p.A), dev(p.MA), batch=3)
     f2 = cs.prepare_fixed(dev(p.A), dev(p.MA), batch=17)
+    # odd batches round down to even: masks of rotations 2k, 2k+1 share a transform
+    assert (f1.batch, f2.batch) == (2, 16)
     a1 = [t.cpu().numpy() for t in f1.score_rotations(dev(p.B), dev(p.MB), quats)]
     a2 = [t.cpu().numpy() for t in f2.score_rotations(dev(p.B), dev(p.MB), quats)]
     np.testing.assert_array_equal(a1[0], a2[0])
@@ -246,3 +248,23 @@ def test_unsquared_measure_flips_sign_under_negation(cs):
     fin = np.isfinite(m1)
     np.testing.assert_array_equal(fin, np.isfinite(m2))
     np.testing.assert_allclose(m2[fin], -m1[fin], rtol=0, atol=1e-6)
+
+
+# ------------------------------------------------------------ BF16 storage form
+TAU_BF16 = 1e-2
+
+
+@pytest.mark.parametrize("dims,pad", [((12, 10, 14), None), ((20, 17, 23), None), ((16, 15, 14), (320, 320, 320))])
+def test_bf16_form_within_reduced_precision_tolerance(cs, dims, pad):
+    p = synth.small_pair(331 + sum(dims), dims, masks="threshold")
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, precision="bf16")
+    worst = 0.0
+    for q in (IDENTITY, p.q_true, rand_quat(3)):
+        gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad)
+        worst = max(worst, check_maps(omap, gmap, tau=TAU_BF16))
+    sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+    for r, q in enumerate(p.quats):
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad)
+        check_best_against_map(omap, sc[r], sh[r], tau=TAU_BF16)
+    assert worst > 0.0          # the reduced-precision path really differs from FP32 arithmetic
