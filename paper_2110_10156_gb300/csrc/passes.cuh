@@ -267,6 +267,9 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
                                               // each thread reads back only its own slots
   float2* stage = ycarry + TILE;              // [H][NT] next field's inputs (own slots)
   float2* tws = stage + H * NT;               // [P] twiddles
+  // a transformed column stays in the exchange slots of the four-step split:
+  // X[kz] with kz = k1 + N1*k2 sits at k2*RS + k1
+  auto slot = [](int kz) { return (kz / N1) * FS::RS + kz % N1; };
   const int t = threadIdx.x;
   const int kx = blockIdx.y, ky0 = blockIdx.x * W;
   const int mkx = (g.Px - kx) % g.Px;
@@ -356,12 +359,13 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
                                                //  before the next copies into its slots)
       if (j + 1 < nfr) fetch(r, j + 1);        // next field's copies overlap this one's work
       else if (r + 1 < nrot) fetch(r + 1, 0);
-      float2 u[N2];
-      if (has2) FS::template step2<-1>(u, ex + c2 * CS, k1);
-      __syncthreads();
       if (has2) {
+        // in place: the outputs X[k1 + N1*k2] go to the slots k2*RS + k1 this
+        // thread has just read, so no other thread's reads are overtaken
+        float2 u[N2];
+        FS::template step2<-1>(u, ex + c2 * CS, k1);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) ex[c2 * CS + k1 + N1 * k2] = u[k2];
+        for (int k2 = 0; k2 < N2; ++k2) ex[c2 * CS + k2 * FS::RS + k1] = u[k2];
       }
       __syncthreads();
       // Eq. 7-8: the weighted channel products (separated through the mirror
@@ -374,8 +378,8 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
           const int i = t + NT * m;
           if (i < TILE) {
             const int c = i / P, kz = i - c * P;
-            const float2 h = ex[c * CS + kz];
-            const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
+            const float2 h = ex[c * CS + slot(kz)];
+            const float2 hm = cconj(ex[(W + c) * CS + slot(kz == 0 ? 0 : P - kz)]);
             X[m] = cadd(X[m], cadd(cmul(Us[i], h), cmul(Vs[i], hm)));
           }
         }
@@ -387,8 +391,8 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
           const int i = t + NT * m;
           if (i < TILE) {
             const int c = i / P, kz = i - c * P;
-            const float2 h = ex[c * CS + kz];
-            const float2 hm = cconj(ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)]);
+            const float2 h = ex[c * CS + slot(kz)];
+            const float2 hm = cconj(ex[(W + c) * CS + slot(kz == 0 ? 0 : P - kz)]);
             const float2 U = Ms[i];
             Y[m] = cmul(U, cscale(cadd(h, hm), 0.5f));
             const float2 d = cscale(csub(h, hm), 0.5f);
@@ -411,15 +415,15 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
       const int i = t + NT * m;
       if (i < TILE) {
         const int c = i / P, kz = i - c * P;
-        ex[c * CS + kz] = make_float2(X[m].x - Y[m].y, X[m].y + Y[m].x);
-        ex[(W + c) * CS + (kz == 0 ? 0 : P - kz)] = make_float2(X[m].x + Y[m].y, Y[m].x - X[m].y);
+        ex[c * CS + slot(kz)] = make_float2(X[m].x - Y[m].y, X[m].y + Y[m].x);
+        ex[(W + c) * CS + slot(kz == 0 ? 0 : P - kz)] = make_float2(X[m].x + Y[m].y, Y[m].x - X[m].y);
       }
     }
     __syncthreads();
     {
       float2 v[N1];
 #pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) v[n1] = ex[c1 * CS + N2 * n1 + n2];
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = ex[c1 * CS + slot(N2 * n1 + n2)];
       __syncthreads();
       FS::template step1<1, true>(v, ex + c1 * CS, n2, tws);
     }
