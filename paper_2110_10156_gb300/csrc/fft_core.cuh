@@ -73,6 +73,7 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // a * (S i)
 template <int S>
@@ -210,13 +211,15 @@ template <> struct Split<320> { static constexpr int N1 = 16, N2 = 20; };
 template <> struct Split<400> { static constexpr int N1 = 16, N2 = 25; };
 template <> struct Split<512> { static constexpr int N1 = 16, N2 = 32; };
 
-template <int N>
+template <int N, bool PAD_ROWS = true>
 struct FourStep {
   static constexpr int N1 = Split<N>::N1;
   static constexpr int N2 = Split<N>::N2;
   // exchange layout per sequence: [n2][k1] with padded strides (odd strides keep
-  // 16 consecutive lanes on distinct bank pairs for either lane ordering)
-  static constexpr int RS = (N1 % 2 == 0) ? N1 + 1 : N1;
+  // 16 consecutive lanes on distinct bank pairs for either lane ordering).
+  // Without row padding (RS = N1) a transformed sequence is in natural order;
+  // that suits callers whose lanes run over sequences (the odd CS spreads them).
+  static constexpr int RS = (PAD_ROWS && N1 % 2 == 0) ? N1 + 1 : N1;
   static constexpr int CS0 = N2 * RS;
   static constexpr int CS = (CS0 % 2 == 0) ? CS0 + 1 : CS0;
   static_assert(CS >= N, "sequence stride must hold N natural-order values");

@@ -234,11 +234,13 @@ struct ZmacCfg {
   // (7 * W * P complex values) stays in shared memory for the whole batch
   static constexpr int W = P <= 320 ? 8 : 4;
   static constexpr int NT = 2 * W * Split<P>::N2;
+  // exchange rows unpadded when 16 columns fill a half-warp (natural order)
+  static constexpr bool PAD = 2 * W < 16;
+  using FS = FourStep<P, PAD>;
   // shared memory: fixed-spectra tile [7][W][P], transform exchange [2W][CS],
-  // the mask product of the odd rotation of a pair [W][P], the next field's
-  // inputs [N1/2][NT] and the twiddle table [P]
+  // two stages of field inputs [2][N1/2][NT] and the twiddle table [P]
   static constexpr size_t smem_bytes =
-      ((size_t)8 * W * P + (size_t)2 * W * FourStep<P>::CS + (size_t)(Split<P>::N1 / 2) * NT + P) *
+      ((size_t)7 * W * P + (size_t)2 * W * FS::CS + (size_t)2 * (Split<P>::N1 / 2) * NT + P) *
       sizeof(float2);
   // Registers per thread when B blocks share an SM: each of the SM's four
   // sub-partitions holds 16384 registers and the warps placed on it, at most
@@ -255,7 +257,7 @@ template <int P, bool BF>
 __global__ void __launch_bounds__(ZmacCfg<P>::NT, ZmacCfg<P>::MIN_BLOCKS)
 k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot, const int* __restrict__ bounds) {
-  using FS = FourStep<P>;
+  using FS = typename ZmacCfg<P>::FS;
   constexpr int W = ZmacCfg<P>::W;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
   constexpr int NC = 2 * W, NT = ZmacCfg<P>::NT, MI = (W * P + NT - 1) / NT;
@@ -263,10 +265,9 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   extern __shared__ float2 smem[];
   float2* uvs = smem;                         // [7][W][P] fixed-spectra weights
   float2* ex = smem + 7 * TILE;               // [NC][CS] transform exchange
-  float2* ycarry = ex + NC * CS;              // [W][P] Y of the odd rotation of a pair;
-                                              // each thread reads back only its own slots
-  float2* stage = ycarry + TILE;              // [H][NT] next field's inputs (own slots)
-  float2* tws = stage + H * NT;               // [P] twiddles
+  float2* stage = ex + NC * CS;               // [2][H][NT] inputs of the next two fields
+                                              // (each thread uses only its own slots)
+  float2* tws = stage + 2 * H * NT;           // [P] twiddles
   // a transformed column stays in the exchange slots of the four-step split:
   // X[kz] with kz = k1 + N1*k2 sits at k2*RS + k1
   auto slot = [](int kz) { return (kz / N1) * FS::RS + kz % N1; };
@@ -289,47 +290,54 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   const bool has2 = t < NC * N1;
   const int c2 = t % NC, k1 = t / NC;
 
-  // z = N2*n1 + n2 < nz <= P/2 only for n1 < N1/2.  The next field's inputs
-  // are copied asynchronously into this thread's own stage slots (cp.async):
-  // no registers are held while the current field is transformed.  Slots
-  // outside the volume are zero once and never copied to.
+  // z = N2*n1 + n2 < nz <= P/2 only for n1 < N1/2.  Field inputs are copied
+  // asynchronously (cp.async) two fields ahead into this thread's own slots of
+  // two stages: no registers are held meanwhile.  Slots outside the volume are
+  // zero once and never copied to.  Fields run in the order (r, j), j < nfr(r).
 #pragma unroll
   for (int n1 = 0; n1 < H; ++n1) {
     const int z = N2 * n1 + n2;
-    if (!(ok1 && z < g.nz)) stage[n1 * NT + t] = make_float2(0.f, 0.f);
+    if (!(ok1 && z < g.nz)) stage[n1 * NT + t] = stage[(H + n1) * NT + t] = make_float2(0.f, 0.f);
   }
-  auto fetch = [&](int r, int j) {
-    const char* src = Fields<BF>::field(F1, g, g.nz * plane_stride, r, j);
-    if (!BF || j == g.nch) {
+  auto nfr = [&](int r) { return (r & 1) ? g.nch : g.nf; };  // an odd rotation's mask came with its partner
+  int pr = 0, pj = 0;                         // next field to copy
+  auto fetch = [&](float2* buf) {             // copies field (pr, pj), if any, and advances
+    if (pr < nrot) {
+      const char* src = Fields<BF>::field(F1, g, g.nz * plane_stride, pr, pj);
+      if (!BF || pj == g.nch) {
 #pragma unroll
-      for (int n1 = 0; n1 < H; ++n1) {
-        const int z = N2 * n1 + n2;
-        if (ok1 && z < g.nz)
-          cp_async8(stage + n1 * NT + t, src + (col_off + (long long)z * g.Py) * 8);
-      }
-    } else {
+        for (int n1 = 0; n1 < H; ++n1) {
+          const int z = N2 * n1 + n2;
+          if (ok1 && z < g.nz)
+            cp_async8(buf + n1 * NT + t, src + (col_off + (long long)z * g.Py) * 8);
+        }
+      } else {
 #pragma unroll
-      for (int n1 = 0; n1 < H; ++n1) {
-        const int z = N2 * n1 + n2;
-        if (ok1 && z < g.nz)
-          cp_async4(stage + n1 * NT + t, src + (col_off + (long long)z * g.Py) * 4);
+        for (int n1 = 0; n1 < H; ++n1) {
+          const int z = N2 * n1 + n2;
+          if (ok1 && z < g.nz)
+            cp_async4(buf + n1 * NT + t, src + (col_off + (long long)z * g.Py) * 4);
+        }
       }
+      if (++pj == nfr(pr)) { pj = 0; ++pr; }
     }
-    cp_async_commit();
+    cp_async_commit();                         // one group per call, empty or not
   };
-  // this thread's staged inputs of field j (after its copies have landed)
-  auto take = [&](float2 (&v)[H], int j) {
-    cp_async_wait_all();
+  // this thread's staged inputs of field j from buf, once all but the most
+  // recent copy group have landed
+  auto take = [&](float2 (&v)[H], const float2* buf, int j) {
+    cp_async_wait_one();
     if (!BF || j == g.nch) {
 #pragma unroll
-      for (int n1 = 0; n1 < H; ++n1) v[n1] = stage[n1 * NT + t];
+      for (int n1 = 0; n1 < H; ++n1) v[n1] = buf[n1 * NT + t];
     } else {
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1)
-        v[n1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(stage + n1 * NT + t));
+        v[n1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(buf + n1 * NT + t));
     }
   };
-  if (nrot > 0) fetch(0, 0);
+  fetch(stage);
+  fetch(stage + H * NT);
 
   for (int q = t; q < P; q += NT) tws[q] = __ldg(&tw[q]);
   // the block's fixed-spectra tile: 7 contiguous runs of W*P values (rows
@@ -345,20 +353,26 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   }
   __syncthreads();                            // twiddles and tile visible to all
 
+  // Y of an odd rotation is formed with its partner's mask field and carried
+  // in Yn: live only from that product to the next rotation's start
+  float2 Y[MI], Yn[MI];
+  int f = 0;                                  // field counter: stage f & 1
   for (int r = 0; r < nrot; ++r) {
-    float2 X[MI], Y[MI];
+    float2 X[MI];
 #pragma unroll
-    for (int m = 0; m < MI; ++m) X[m] = Y[m] = make_float2(0.f, 0.f);
-    const int nfr = (r & 1) ? g.nch : g.nf;   // an odd rotation's mask came with its partner
+    for (int m = 0; m < MI; ++m) {
+      X[m] = make_float2(0.f, 0.f);
+      Y[m] = (r & 1) ? Yn[m] : make_float2(0.f, 0.f);
+    }
 #pragma unroll 1
-    for (int j = 0; j < nfr; ++j) {
+    for (int j = 0; j < nfr(r); ++j, ++f) {
+      float2* buf = stage + (f & 1) * H * NT;
       float2 v[H];
-      take(v, j);
+      take(v, buf, j);
       FS::template step1_half<-1, true>(v, ex + c1 * CS, n2, tws);
-      __syncthreads();                         // (also orders this thread's stage reads
-                                               //  before the next copies into its slots)
-      if (j + 1 < nfr) fetch(r, j + 1);        // next field's copies overlap this one's work
-      else if (r + 1 < nrot) fetch(r + 1, 0);
+      __syncthreads();                         // (also orders this thread's reads of buf
+                                               //  before the next copies into it)
+      fetch(buf);                              // two fields ahead
       if (has2) {
         // in place: the outputs X[k1 + N1*k2] go to the slots k2*RS + k1 this
         // thread has just read, so no other thread's reads are overtaken
@@ -396,18 +410,11 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
             const float2 U = Ms[i];
             Y[m] = cmul(U, cscale(cadd(h, hm), 0.5f));
             const float2 d = cscale(csub(h, hm), 0.5f);
-            ycarry[i] = cmul(U, make_float2(d.y, -d.x));
+            Yn[m] = cmul(U, make_float2(d.y, -d.x));
           }
         }
       }
       __syncthreads();
-    }
-    if (r & 1) {
-#pragma unroll
-      for (int m = 0; m < MI; ++m) {
-        const int i = t + NT * m;
-        if (i < TILE) Y[m] = ycarry[i];
-      }
     }
     // Z = X + iY at k, conj(X) + i conj(Y) at -k
 #pragma unroll
