@@ -262,7 +262,7 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
   constexpr int NC = 2 * W, NT = ZmacCfg<P>::NT, MI = (W * P + NT - 1) / NT;
   constexpr int TILE = W * P;                 // complex values per fixed-spectra tile
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   float2* uvs = smem;                         // [7][W][P] fixed-spectra weights
   float2* ex = smem + 7 * TILE;               // [NC][CS] transform exchange
   float2* stage = ex + NC * CS;               // [2][H][NT] inputs of the next two fields
@@ -336,22 +336,26 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
         v[n1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(buf + n1 * NT + t));
     }
   };
-  fetch(stage);
-  fetch(stage + H * NT);
-
-  for (int q = t; q < P; q += NT) tws[q] = __ldg(&tw[q]);
   // the block's fixed-spectra tile: 7 contiguous runs of W*P values (rows
-  // ky0..ky0+W-1 are contiguous in [kx][ky][kz]); rows past Py are zero
+  // ky0..ky0+W-1 are contiguous in [kx][ky][kz]), copied asynchronously as the
+  // first copy group; rows past Py are zero
   {
     const int valid = min(W, g.Py - ky0) * P;
     for (int a = 0; a < 2 * g.nch + 1; ++a) {
-      const float4* src = reinterpret_cast<const float4*>(UV + a * S7 + ((long long)kx * g.Py + ky0) * P);
-      float4* dst = reinterpret_cast<float4*>(uvs + a * TILE);
-      for (int q = t; q < TILE / 2; q += NT)
-        dst[q] = (2 * q < valid) ? __ldg(&src[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float2* src = UV + a * S7 + ((long long)kx * g.Py + ky0) * P;
+      float2* dst = uvs + a * TILE;
+      for (int q = t; q < TILE / 2; q += NT) {
+        if (2 * q < valid) cp_async16(dst + 2 * q, src + 2 * q);
+        else reinterpret_cast<float4*>(dst)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
+    cp_async_commit();
   }
-  __syncthreads();                            // twiddles and tile visible to all
+  fetch(stage);
+  fetch(stage + H * NT);
+  for (int q = t; q < P; q += NT) tws[q] = __ldg(&tw[q]);
+  __syncthreads();                            // twiddles visible to all (the tile is
+                                              // waited for with the first field)
 
   // Y of an odd rotation is formed with its partner's mask field and carried
   // in Yn: live only from that product to the next rotation's start
