@@ -238,10 +238,13 @@ struct ZmacCfg {
   static constexpr bool PAD = 2 * W < 16;
   using FS = FourStep<P, PAD>;
   // shared memory: fixed-spectra tile [7][W][P], transform exchange [2W][CS],
-  // two stages of field inputs [2][N1/2][NT] and the twiddle table [P]
-  static constexpr size_t smem_bytes =
-      ((size_t)7 * W * P + (size_t)2 * W * FS::CS + (size_t)2 * (Split<P>::N1 / 2) * NT + P) *
-      sizeof(float2);
+  // two stages of field inputs [2][N1/2][NT] and, where it does not cost a
+  // second block per SM, the twiddle table [P] (else twiddles come from L1)
+  static constexpr size_t smem_base =
+      ((size_t)7 * W * P + (size_t)2 * W * FS::CS + (size_t)2 * (Split<P>::N1 / 2) * NT) * sizeof(float2);
+  static constexpr bool fits2(size_t b) { return 2 * (b + 1024) <= 228 * 1024; }   // per-block reserve
+  static constexpr bool TWS = fits2(smem_base + P * sizeof(float2)) || !fits2(smem_base);
+  static constexpr size_t smem_bytes = smem_base + (TWS ? P * sizeof(float2) : 0);
   // Registers per thread when B blocks share an SM: each of the SM's four
   // sub-partitions holds 16384 registers and the warps placed on it, at most
   // ceil(B * warps / 4) of them (allocation in multiples of 8 per thread).
@@ -250,7 +253,7 @@ struct ZmacCfg {
   }
   // two blocks per SM where shared memory allows it and each thread still
   // keeps at least 128 registers
-  static constexpr int MIN_BLOCKS = (2 * smem_bytes <= 220 * 1024 && regs_for(2) >= 128) ? 2 : 1;
+  static constexpr int MIN_BLOCKS = (fits2(smem_bytes) && regs_for(2) >= 128) ? 2 : 1;
 };
 
 template <int P, bool BF>
@@ -353,7 +356,10 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   }
   fetch(stage);
   fetch(stage + H * NT);
-  for (int q = t; q < P; q += NT) tws[q] = __ldg(&tw[q]);
+  constexpr bool TWS = ZmacCfg<P>::TWS;
+  if constexpr (TWS)
+    for (int q = t; q < P; q += NT) tws[q] = __ldg(&tw[q]);
+  const float2* twz = TWS ? tws : tw;
   __syncthreads();                            // twiddles visible to all (the tile is
                                               // waited for with the first field)
 
@@ -373,7 +379,7 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
       float2* buf = stage + (f & 1) * H * NT;
       float2 v[H];
       take(v, buf, j);
-      FS::template step1_half<-1, true>(v, ex + c1 * CS, n2, tws);
+      FS::template step1_half<-1, TWS>(v, ex + c1 * CS, n2, twz);
       __syncthreads();                         // (also orders this thread's reads of buf
                                                //  before the next copies into it)
       fetch(buf);                              // two fields ahead
@@ -436,7 +442,7 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
 #pragma unroll
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = ex[c1 * CS + slot(N2 * n1 + n2)];
       __syncthreads();
-      FS::template step1<1, true>(v, ex + c1 * CS, n2, tws);
+      FS::template step1<1, TWS>(v, ex + c1 * CS, n2, twz);
     }
     __syncthreads();
     if (has2 && !(c2 >= W && self_mirror)) {
