@@ -147,8 +147,28 @@ void launch_fwd_x(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw
 // is transposed so that ky is contiguous for the z pass.
 // Block: W consecutive kx of one (r, j, z) plane.
 // ---------------------------------------------------------------------------
+// Blocks per SM for the single-transform passes: as many as keep at least
+// MINR registers per thread (each of the SM's four sub-partitions holds 16384
+// registers for the warps placed on it) and fit in shared memory.
+constexpr int pass_blocks(int threads, size_t smem, int minr) {
+  int best = 1;
+  for (int b = 2; b <= 8; ++b) {
+    const int per_sub = (b * ((threads + 31) / 32) + 3) / 4;
+    const int regs = (16384 / (32 * per_sub)) / 8 * 8;
+    if (regs >= minr && (size_t)b * (smem + 1024) <= 228 * 1024) best = b;
+  }
+  return best;
+}
+template <int P> struct FwdYCfg {
+  static constexpr int W = 16;
+  static constexpr int NT = W * Split<P>::N2;
+  static constexpr size_t smem_bytes = (size_t)W * FourStep<P>::CS * sizeof(float2);
+  // the 25- and 32-point second stages need more registers than 16- or 20-point ones
+  static constexpr int MIN_BLOCKS = pass_blocks(NT, smem_bytes, Split<P>::N2 > 20 ? 80 : 48);
+};
+
 template <int P, int W, bool BF>
-__global__ void __launch_bounds__(W * Split<P>::N2)
+__global__ void __launch_bounds__(W * Split<P>::N2, FwdYCfg<P>::MIN_BLOCKS)
 k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __restrict__ tw,
         Geo g) {
   using FS = FourStep<P>;
@@ -207,8 +227,8 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
 
 template <int P>
 void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, cudaStream_t st) {
-  constexpr int W = 16, N2 = Split<P>::N2;
-  const size_t smem = (size_t)W * FourStep<P>::CS * sizeof(float2);
+  constexpr int W = FwdYCfg<P>::W, N2 = Split<P>::N2;
+  const size_t smem = FwdYCfg<P>::smem_bytes;
   dim3 grid((unsigned)(nrot * g.nf * g.nz), (unsigned)((g.Px + W - 1) / W));
   if (g.bf16) {
     set_smem(k_fwd_y<P, W, true>, smem);
