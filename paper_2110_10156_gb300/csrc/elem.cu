@@ -84,53 +84,74 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
   }
 }
 
-// Section 3.2 resample.  Block: 8 x 4 x 4 voxels (x fastest), so one warp's
-// sample points form a compact rotated 8 x 4 patch.
+// Section 3.2 resample.  Block: 8 x 4 voxels per warp (x fastest), so one
+// warp's sample points form a compact rotated 8 x 4 patch; four warps take
+// four consecutive z-planes, and each thread repeats that for RZ plane groups
+// (block: 8 x 4 x 4*RZ voxels).  Mask counts per axis (the slab bound's
+// marginals) are reduced with warp shuffles before one atomic per slot.
 // Grid: (x tiles, y tiles, z tiles * rotations).
 __global__ void __launch_bounds__(128)
 k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
            float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
            int* __restrict__ marg) {
-  const int ztiles = (g.nz + 3) / 4;
+  constexpr int RZ = kResampleZGroups, ZB = 4 * RZ;    // z-planes per block
+  const int ztiles = (g.nz + ZB - 1) / ZB;
   const int r = blockIdx.z / ztiles, zt = blockIdx.z - r * ztiles;
-  const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 3, tz = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int tx = lane & 7, ty = lane >> 3;
   const int x = blockIdx.x * 8 + tx;
   const int y = blockIdx.y * 4 + ty;
-  const int z = zt * 4 + tz;
-  __shared__ int slab[16];                    // 4 z-planes, 4 y-rows, 8 x-columns
-  if (threadIdx.x < 16) slab[threadIdx.x] = 0;
-  __syncthreads();
-  int count = 0;
-  if (x < g.nx && y < g.ny && z < g.nz) {
-    float val;
-    uint8_t m;
-    resample_voxel(BM, rot[r], g, x, y, z, val, m);
-    const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
-    Bh[idx] = val;
-    Mh[idx] = m;
-    count = m;
-    if (m && marg) {
-      atomicAdd_block(&slab[tz], 1);
-      atomicAdd_block(&slab[4 + ty], 1);
-      atomicAdd_block(&slab[8 + tx], 1);
+  __shared__ int zs[ZB], ys[4][4], xs[4][8], cs[4];
+  const RotMat R = rot[r];
+  int c = 0;                                   // this thread's mask voxels
+#pragma unroll 1
+  for (int k = 0; k < RZ; ++k) {
+    const int z = zt * ZB + 4 * k + wid;
+    int mk = 0;
+    if (x < g.nx && y < g.ny && z < g.nz) {
+      float val;
+      uint8_t m;
+      resample_voxel(BM, R, g, x, y, z, val, m);
+      const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
+      Bh[idx] = val;
+      Mh[idx] = m;
+      mk = m;
     }
+    c += mk;
+    const int wz = __reduce_add_sync(0xffffffffu, mk);      // plane z, this warp's patch
+    if (lane == 0) zs[4 * k + wid] = wz;
   }
-  // block reduction of the mask count
-  for (int off = 16; off > 0; off >>= 1) count += __shfl_down_sync(0xffffffffu, count, off);
-  __shared__ int warp_sums[4];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) warp_sums[wid] = count;
+  int cy = c;                                  // lanes sharing ty: xor over the tx bits
+  cy += __shfl_xor_sync(0xffffffffu, cy, 1);
+  cy += __shfl_xor_sync(0xffffffffu, cy, 2);
+  cy += __shfl_xor_sync(0xffffffffu, cy, 4);
+  int cx = c;                                  // lanes sharing tx: xor over the ty bits
+  cx += __shfl_xor_sync(0xffffffffu, cx, 8);
+  cx += __shfl_xor_sync(0xffffffffu, cx, 16);
+  if (tx == 0) ys[wid][ty] = cy;
+  if (ty == 0) xs[wid][tx] = cx;
+  const int cw = __reduce_add_sync(0xffffffffu, c);
+  if (lane == 0) cs[wid] = cw;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int c = warp_sums[0] + warp_sums[1] + warp_sums[2] + warp_sums[3];
-    if (c) atomicAdd(&msum[r], c);
+  const int t = threadIdx.x;
+  if (t == 0) {
+    const int total = cs[0] + cs[1] + cs[2] + cs[3];
+    if (total) atomicAdd(&msum[r], total);
   }
-  if (marg && threadIdx.x < 16 && slab[threadIdx.x]) {
+  if (marg) {
     int* mr = marg + (long long)r * (g.nz + g.ny + g.nx);
-    const int t = threadIdx.x;
-    if (t < 4) atomicAdd(&mr[zt * 4 + t], slab[t]);
-    else if (t < 8) atomicAdd(&mr[g.nz + blockIdx.y * 4 + (t - 4)], slab[t]);
-    else atomicAdd(&mr[g.nz + g.ny + blockIdx.x * 8 + (t - 8)], slab[t]);
+    if (t < ZB) {                              // z = zt*ZB + t (4k + wid = t)
+      const int v = zs[t];
+      if (v) atomicAdd(&mr[zt * ZB + t], v);
+    } else if (t < ZB + 4) {
+      const int q = t - ZB;
+      const int v = ys[0][q] + ys[1][q] + ys[2][q] + ys[3][q];
+      if (v) atomicAdd(&mr[g.nz + blockIdx.y * 4 + q], v);
+    } else if (t < ZB + 12) {
+      const int q = t - ZB - 4;
+      const int v = xs[0][q] + xs[1][q] + xs[2][q] + xs[3][q];
+      if (v) atomicAdd(&mr[g.nz + g.ny + blockIdx.x * 8 + q], v);
+    }
   }
 }
 

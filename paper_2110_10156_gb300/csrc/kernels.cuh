@@ -93,9 +93,10 @@ __global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict
 __global__ void k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
                            float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
                            int* __restrict__ marg);
+constexpr int kResampleZGroups = 4;            // z-plane groups of 4 per resample block
 inline dim3 resample_grid(const Geo& g, int nrot) {
   return dim3((unsigned)((g.nx + 7) / 8), (unsigned)((g.ny + 3) / 4),
-              (unsigned)(((g.nz + 3) / 4) * nrot));
+              (unsigned)(((g.nz + 4 * kResampleZGroups - 1) / (4 * kResampleZGroups)) * nrot));
 }
 
 // ----------------------------------------------------------------- shift bounds
