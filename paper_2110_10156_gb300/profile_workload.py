@@ -15,13 +15,73 @@ import sys
 import numpy as np
 
 
+STAGE_OF = {"k_resample": "resample", "k_fwd_x": "fwd_x", "k_fwd_y": "fwd_y", "k_zmac": "zmac",
+            "k_inv_y": "inv_y", "k_inv_x": "inv_x"}
+
+
+def traffic_from_csv(csv_path: str, rotations: int, out_path: str) -> dict:
+    """DRAM bytes per rotation of each scoring stage from an ncu CSV log of one
+    scored group (metrics dram__bytes_read.sum, dram__bytes_write.sum), keyed by
+    the current kernel-source hash so a stale file is ignored."""
+    import csv
+    import json
+    import os
+
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    per = {}
+    with open(csv_path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    rows = list(csv.DictReader(lines))
+
+    def stage_of(name):
+        head = name.split("(")[0].split("<")[0]
+        return next((v for k, v in STAGE_OF.items() if head == k or head.endswith("::" + k)
+                     or head.endswith(" " + k)), None)
+
+    # the fixed volume's own x and y passes come before the first resample
+    first = min((int(r["ID"]) for r in rows if stage_of(r.get("Kernel Name", "")) == "resample"),
+                default=0)
+    for r in rows:
+        stage = stage_of(r.get("Kernel Name", ""))
+        if stage is None or int(r["ID"]) < first:
+            continue
+        if r.get("Metric Name") not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        v = float(r["Metric Value"].replace(",", "")) * scale.get(r.get("Metric Unit", "byte"), 1.0)
+        per.setdefault(stage, {}).setdefault(r["ID"], 0.0)
+        per[stage][r["ID"]] += v
+    import importlib.util
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    out = {"src_hash": bench.kernel_source_hash(),
+           "source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {rotations} rotations "
+                     f"in one launch group ({os.path.basename(csv_path)})",
+           "stages": {k: {"launches": len(v), "dram_bytes_per_rotation": sum(v.values()) / rotations}
+                      for k, v in sorted(per.items())}}
+    with open(out_path, "w") as fh:
+        json.dump(out, fh, indent=1)
+        fh.write("\n")
+    return out
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
+    ap.add_argument("--traffic-from", help="summarise an ncu CSV log into profiles/ncu_traffic.json")
     ap.add_argument("--size", type=int, default=150)
     ap.add_argument("--rotations", type=int, default=2)
     ap.add_argument("--batch", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args(argv)
+    if args.traffic_from:
+        import json
+        import os
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        out = traffic_from_csv(args.traffic_from, args.rotations,
+                               os.path.join(root, "profiles", "ncu_traffic.json"))
+        print(json.dumps(out, indent=1))
+        return 0
 
     import torch
 
