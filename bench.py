@@ -124,24 +124,31 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ byte model
-def stage_bytes(dims, pad, nb, stage, nf=4):
-    """Algorithmic HBM bytes of one launch that scores nb rotations (nf packed
-    fields per rotation: 4 for the squared measure)."""
+def stage_bytes(dims, pad, nb, stage, nch=3, precision="fp32"):
+    """Algorithmic HBM bytes of one launch that scores nb rotations.
+
+    nch packed channel fields per rotation (3 for the squared measure; BF16 or
+    FP32 storage) plus one mask field per pair of rotations (FP32).  The z pass
+    counts its field reads and the fixed-spectra tile it loads once per launch;
+    its output planes and the inverse passes' traffic depend on the slab bound
+    and are left out of the z pass (a lower bound) and counted unpruned for the
+    two inverse passes (an upper bound)."""
     nz, ny, nx = dims
     Pz, Py, Px = pad
     vz, vy = 2 * nz - 1, 2 * ny - 1
     nvox = nz * ny * nx
-    c8 = 8
-    F0 = nf * nz * ny * Px * c8
-    F1 = nf * nz * Px * Py * c8
-    F2 = vz * Px * Py * c8
-    F3 = vz * vy * Px * c8
-    UV = (2 * nf - 1) * (Px // 2 + 1) * Py * Pz * c8
+    cb = 4 if precision == "bf16" else 8
+    per_elem = nch * nb * cb + ((nb + 1) // 2) * 8     # bytes per element position, all fields
+    F0 = per_elem * nz * ny * Px
+    F1 = per_elem * nz * Px * Py
+    F2 = vz * Px * Py * 8
+    F3 = vz * vy * Px * 8
+    UV = (2 * nch + 1) * (Px // 2 + 1) * Py * Pz * 8
     return {
-        "resample": nvox * 5 + nb * nvox * 5,
-        "fwd_x": nb * (nvox * 5 + F0),
-        "fwd_y": nb * (F0 + F1),
-        "zmac": nb * (F1 + F2) + UV,
+        "resample": nb * nvox * 5,
+        "fwd_x": nb * nvox * 5 + F0,
+        "fwd_y": F0 + F1,
+        "zmac": F1 + UV,
         "inv_y": nb * (F2 + F3),
         "inv_x": nb * F3,
     }.get(stage, 0)
@@ -166,16 +173,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(stage: str):
+def ncu_traffic(stage: str, precision: str = "fp32"):
     """DRAM bytes per rotation for a stage from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+    was taken on the current kernel sources in the same precision; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except Exception:
         return None
-    if d.get("src_hash") != kernel_source_hash():
+    if d.get("src_hash") != kernel_source_hash() or d.get("precision", "fp32") != precision:
         return None
     e = d.get("stages", {}).get(stage)
     return None if e is None else float(e["dram_bytes_per_rotation"])
@@ -367,10 +374,10 @@ def run_ours(args):
     total_bytes = 0
     for b in range(nbatches):
         nb = min(f.batch, R - b * f.batch)
-        total_bytes += stage_bytes(dims, pad, nb, dom)
+        total_bytes += stage_bytes(dims, pad, nb, dom, precision=args.precision)
     total_bytes *= prof_steps
     achieved = total_bytes / (stage_ms[dom] / 1000.0) / 1e9 if stage_ms[dom] > 0 else 0.0
-    tr = ncu_traffic(dom)
+    tr = ncu_traffic(dom, args.precision)
     per_launch_rot = R / nbatches
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",

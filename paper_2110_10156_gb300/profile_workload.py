@@ -19,7 +19,7 @@ STAGE_OF = {"k_resample": "resample", "k_fwd_x": "fwd_x", "k_fwd_y": "fwd_y", "k
             "k_inv_y": "inv_y", "k_inv_x": "inv_x"}
 
 
-def traffic_from_csv(csv_path: str, rotations: int, out_path: str) -> dict:
+def traffic_from_csv(csv_path: str, rotations: int, out_path: str, precision: str = "fp32") -> dict:
     """DRAM bytes per rotation of each scoring stage from an ncu CSV log of one
     scored group (metrics dram__bytes_read.sum, dram__bytes_write.sum), keyed by
     the current kernel-source hash so a stale file is ignored."""
@@ -55,7 +55,7 @@ def traffic_from_csv(csv_path: str, rotations: int, out_path: str) -> dict:
     spec = importlib.util.spec_from_file_location("bench", os.path.join(root, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
-    out = {"src_hash": bench.kernel_source_hash(),
+    out = {"src_hash": bench.kernel_source_hash(), "precision": precision,
            "source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {rotations} rotations "
                      f"in one launch group ({os.path.basename(csv_path)})",
            "stages": {k: {"launches": len(v), "dram_bytes_per_rotation": sum(v.values()) / rotations}
@@ -69,6 +69,7 @@ def traffic_from_csv(csv_path: str, rotations: int, out_path: str) -> dict:
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--traffic-from", help="summarise an ncu CSV log into profiles/ncu_traffic.json")
+    ap.add_argument("--precision", choices=("fp32", "bf16"), default="fp32")
     ap.add_argument("--size", type=int, default=150)
     ap.add_argument("--rotations", type=int, default=2)
     ap.add_argument("--batch", type=int, default=2)
@@ -79,7 +80,7 @@ def main(argv=None) -> int:
         import os
         root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
         out = traffic_from_csv(args.traffic_from, args.rotations,
-                               os.path.join(root, "profiles", "ncu_traffic.json"))
+                               os.path.join(root, "profiles", "ncu_traffic.json"), args.precision)
         print(json.dumps(out, indent=1))
         return 0
 
@@ -91,7 +92,7 @@ def main(argv=None) -> int:
                         max(3.0, 30 * n / 150), 30.0, max(1, int(20 * n / 150)),
                         args.rotations, masks="threshold")
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    f = cs_ngf.prepare_fixed(dev(p.A), dev(p.MA), batch=args.batch)
+    f = cs_ngf.prepare_fixed(dev(p.A), dev(p.MA), batch=args.batch, precision=args.precision)
     B, MB = dev(p.B), dev(p.MB)
     for _ in range(args.repeat):
         sc, sh = f.score_rotations(B, MB, p.quats)
