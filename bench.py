@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -152,6 +153,27 @@ def stage_bytes(dims, pad, nb, stage, nch=3, precision="fp32"):
         "inv_y": nb * (F2 + F3),
         "inv_x": nb * F3,
     }.get(stage, 0)
+
+
+def zmac_flops(pad, nb, nch=3):
+    """Algorithmic flops of one z-pass launch over nb rotations: 5 L log2 L per
+    complex length-L transform (the forward input is zero past L/2, which
+    prunes the first radix-2 stage: 5 L (log2 L - 1) + L), for nch channel
+    fields plus one mask field per pair of rotations over every (kx, ky)
+    column, one inverse per column, and the spectral multiply-accumulate over
+    the kx <= Px/2 half (16 flops per channel field, 20 for the mask pair)."""
+    Pz, Py, Px = pad
+    L = Pz
+    lg = math.log2(L)
+    fwd = 5 * L * (lg - 1) + L
+    inv = 5 * L * lg
+    cols = Px * Py
+    fields = nch * nb + (nb + 1) // 2
+    mac = (Px // 2 + 1) * Py * Pz * (16 * nch + 20) * nb
+    return fields * cols * fwd + nb * cols * inv + mac
+
+
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
 def measured_peaks():
@@ -386,6 +408,15 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": total_bytes / (prof_steps * nbatches),
                 "timing": "CUDA events around every launch of one profiled step after the timed region"}
 
+    roofline_alu = None
+    if dom == "zmac":
+        fl = sum(zmac_flops(pad, min(f.batch, R - b * f.batch)) for b in range(nbatches)) * prof_steps
+        ach = fl / (stage_ms[dom] / 1000.0) / 1e12 if stage_ms[dom] > 0 else 0.0
+        roofline_alu = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": ach / FP32_ALU_PEAK_TFLOPS, "kernel": dom,
+                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                        "flops_per_launch": fl / (prof_steps * nbatches)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = min(host_cores(), 16)
@@ -406,7 +437,7 @@ def run_ours(args):
                        "rotations_per_gpu": R, "batch": f.batch, "masks": "thresholded foreground",
                        "l2": "inputs larger than L2: every step streams >1 TB of FFT intermediates",
                        "step": "update_fixed + score all rotations + max over rotations"},
-            "roofline": roofline,
+            "roofline": roofline, "roofline_alu": roofline_alu,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * R * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
