@@ -625,7 +625,8 @@ def run_serving(args):
         s = SERVE_SHAPES[int(rng.integers(len(SERVE_SHAPES)))]
         R = int(rng.integers(200, 2001))
         jobs.append((s, synth.random_quaternions(rng, R)))
-    srv = cs_ngf.Server(max_active_jobs=args.serve_active, max_inflight=2, batch=args.serve_batch)
+    srv = cs_ngf.Server(max_active_jobs=args.serve_active, max_inflight=2, batch=args.serve_batch,
+                        policy=args.serve_policy)
     # capacity: each shape alone once (also warms the pooled resources)
     svc = {}
     for s in SERVE_SHAPES:
@@ -654,7 +655,8 @@ def run_serving(args):
         "rotations_per_s": rot / wall, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "jobs of 64^3, 96x128x128, 150^3, 192x192x160 with 200-2000 rotations",
                    "jobs": n_jobs, "offered_load": args.serve_load, "arrival_rate_per_s": lam,
-                   "max_active_jobs": args.serve_active, "batch": args.serve_batch},
+                   "max_active_jobs": args.serve_active, "batch": args.serve_batch,
+                   "admission": args.serve_policy},
         "service_ms_per_rotation_alone": {"x".join(map(str, s)): 1000 * v for s, v in svc.items()},
         "statuses": sorted(set(r["status"] for r in res))}), flush=True)
     return 0
@@ -681,6 +683,7 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-active", type=int, default=4)
+    ap.add_argument("--serve-policy", choices=("arrival", "shortest"), default="arrival")
     ap.add_argument("--serve-batch", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "ours" and args.workload != "align150":

@@ -224,9 +224,9 @@ cs_ngf_status cs_ngf_score_rotations_noalloc(const float* A, const uint8_t* mask
 /* ---------------------------------------------------------------------------
  * Serving: a continuous-batching request loop for alignment jobs of mixed
  * sizes (the scoring of Section 3.2 for each job; the paper runs one job at a
- * time).  Jobs arrive at any time.  A worker thread admits them in arrival
- * order while their device footprint fits the memory budget and an active slot
- * is free.  Device resources are pooled by volume shape and reused without
+ * time).  Jobs arrive at any time.  A worker thread admits them (in arrival
+ * order, or shortest expected work first) while their device footprint fits
+ * the memory budget and an active slot is free.  Device resources are pooled by volume shape and reused without
  * reallocation.  The fixed-volume spectra of each active job stay resident.
  * The worker feeds each job's rotations one launch group at a time on the
  * job's own stream (at most max_inflight groups per job, round-robin over the
@@ -235,12 +235,22 @@ cs_ngf_status cs_ngf_score_rotations_noalloc(const float* A, const uint8_t* mask
  * All inputs of cs_ngf_server_submit are HOST arrays, copied during the call. */
 typedef struct cs_ngf_server cs_ngf_server;
 
+/* Admission order when an active slot is free.  ARRIVAL admits pending jobs
+ * in submission order.  SHORTEST admits the pending job with the smallest
+ * estimated work minus the time it has waited (estimated work: rotations x
+ * padded FFT voxels x 2.5e-8 ms, the per-rotation cost measured on one
+ * GB300), so short jobs overtake long ones and a long job's priority grows
+ * while it waits.  Under either order, when the chosen job does not fit the
+ * memory budget no later job is admitted before it. */
+enum { CS_NGF_SERVE_ARRIVAL = 0, CS_NGF_SERVE_SHORTEST = 1 };
+
 typedef struct {
   int64_t memory_budget_bytes;      /* device bytes for job resources; 0 = 80 % of free memory */
   int32_t max_active_jobs;          /* jobs on the GPU at once (default 4) */
   int32_t max_inflight;             /* launch groups in flight per job (default 2) */
   int32_t batch;                    /* rotations per launch group when a job's cfg batch is 0 (default 16) */
-  int32_t reserved_;
+  int32_t policy;                   /* admission order: CS_NGF_SERVE_ARRIVAL (default) or
+                                       CS_NGF_SERVE_SHORTEST */
   int64_t inject_admission_failure; /* test hook: the job with this id fails admission (ENOMEM); 0 = off */
 } cs_ngf_server_config;
 

@@ -58,7 +58,7 @@ class Info(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_int64), ("max_active_jobs", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("batch", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32), ("inject_admission_failure", ctypes.c_int64)]
+                ("policy", ctypes.c_int32), ("inject_admission_failure", ctypes.c_int64)]
 
 
 class JobResult(ctypes.Structure):
@@ -373,14 +373,19 @@ class Server:
     """Continuous-batching request loop (cs_ngf_server_*): submit host arrays,
     wait for per-job results.  Runs on the current CUDA device."""
 
+    POLICIES = {"arrival": 0, "shortest": 1}
+
     def __init__(self, memory_budget_bytes=0, max_active_jobs=4, max_inflight=2, batch=16,
-                 inject_admission_failure=0):
+                 inject_admission_failure=0, policy="arrival"):
+        if policy not in self.POLICIES:
+            raise ValueError(f"policy must be one of {sorted(self.POLICIES)}")
         cfg = ServerConfig()
         _lib.cs_ngf_server_default_config(ctypes.byref(cfg))
         cfg.memory_budget_bytes = int(memory_budget_bytes)
         cfg.max_active_jobs = int(max_active_jobs)
         cfg.max_inflight = int(max_inflight)
         cfg.batch = int(batch)
+        cfg.policy = self.POLICIES[policy]
         cfg.inject_admission_failure = int(inject_admission_failure)
         h = ctypes.c_void_p()
         _check(_lib.cs_ngf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cs_ngf_server_create")

@@ -2,8 +2,9 @@
 //
 // Jobs (a fixed/floating volume pair and a set of candidate rotations, of any
 // supported size) arrive at any time.  A worker thread:
-//   - admits pending jobs in arrival order while their device footprint fits
-//     the memory budget and an active-job slot is free (device resources are
+//   - admits pending jobs, in arrival order or shortest expected work first
+//     (less the time waited), while their device footprint fits the memory
+//     budget and an active-job slot is free (device resources are
 //     pooled by volume shape, so a finished job's memory serves the next job
 //     of that shape without cudaFree / cudaMalloc);
 //   - keeps every active job's fixed-volume spectra resident and feeds its
@@ -74,6 +75,7 @@ struct Job {
   cs_ngf_config cfg{};
   int pad[3] = {0, 0, 0};
   size_t bytes = 0;
+  double est_ms = 0.0;              // estimated device time alone (admission priority)
   Clock::time_point t_submit, t_admit, t_done;
   enum State { PENDING, ACTIVE, DONE } state = PENDING;
   bool cancel = false;
@@ -257,17 +259,25 @@ void worker_loop(cs_ngf_server* sv) {
     if (sv->stop && sv->pending.empty() && sv->active.empty()) break;
     bool progress = false;
 
-    // ---- admission, in arrival order
+    // ---- admission: cancelled jobs leave; then arrival order, or shortest
+    // expected work less the time waited
     for (auto it = sv->pending.begin(); it != sv->pending.end();) {
       Job* j = *it;
-      if (j->cancel) {
-        j->status = CS_NGF_ECANCELED;
-        j->error = "cancelled before admission";
-        it = sv->pending.erase(it);
-        finish_job(sv, j);
-        progress = true;
-        continue;
-      }
+      if (!j->cancel) { ++it; continue; }
+      j->status = CS_NGF_ECANCELED;
+      j->error = "cancelled before admission";
+      it = sv->pending.erase(it);
+      finish_job(sv, j);
+      progress = true;
+    }
+    if (sv->cfg.policy == CS_NGF_SERVE_SHORTEST && sv->pending.size() > 1) {
+      const Clock::time_point now = Clock::now();
+      std::stable_sort(sv->pending.begin(), sv->pending.end(), [&](const Job* a, const Job* b) {
+        return a->est_ms - ms_between(a->t_submit, now) < b->est_ms - ms_between(b->t_submit, now);
+      });
+    }
+    for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+      Job* j = *it;
       if ((int)sv->active.size() >= sv->cfg.max_active_jobs) break;
       bool fresh = false;
       Slot* slot = find_slot(sv, j, &fresh);
@@ -408,6 +418,8 @@ cs_ngf_status cs_ngf_server_create(const cs_ngf_server_config* cfg_in, cs_ngf_se
   if (cfg_in) cfg = *cfg_in;
   if (cfg.max_active_jobs <= 0 || cfg.max_inflight <= 0)
     return fail(CS_NGF_EINVAL, "max_active_jobs and max_inflight must be positive");
+  if (cfg.policy != CS_NGF_SERVE_ARRIVAL && cfg.policy != CS_NGF_SERVE_SHORTEST)
+    return fail(CS_NGF_EINVAL, "unknown admission policy");
   auto* sv = new (std::nothrow) cs_ngf_server();
   if (!sv) return fail(CS_NGF_ENOMEM, "host allocation failed");
   if (cudaGetDevice(&sv->device) != cudaSuccess) {
@@ -444,6 +456,7 @@ cs_ngf_status cs_ngf_server_submit(cs_ngf_server* sv, const float* A, const uint
   if (j->cfg.batch == 0) j->cfg.batch = sv->cfg.batch > 0 ? sv->cfg.batch : 16;
   std::memcpy(j->dims, dims, sizeof(j->dims));
   j->R = R;
+  j->est_ms = (double)R * j->pad[0] * j->pad[1] * j->pad[2] * 2.5e-8;
   j->bytes = slot_bytes(dims, j->pad, j->cfg.batch, j->cfg.measure, j->cfg.precision, R);
   if (j->bytes > (size_t)sv->cfg.memory_budget_bytes)
     return fail(CS_NGF_ENOMEM, "job needs " + std::to_string(j->bytes) + " device bytes, budget is " +

@@ -83,3 +83,20 @@ def test_entry_points_reject_null_handle(binding):
     assert lib.cs_ngf_score_rotations(None, None, None, None, 1, None, None, None) == binding.EINVAL
     assert lib.cs_ngf_get_info(None, None) == binding.EINVAL
     lib.cs_ngf_release(None)
+
+
+def test_server_config_checks_before_touching_the_device(binding):
+    """The ctypes layout matches the header's defaults, and bad settings are
+    refused before any device call (an unknown admission policy included)."""
+    lib = binding.library()
+    cfg = binding.ServerConfig()
+    lib.cs_ngf_server_default_config(ctypes.byref(cfg))
+    assert (cfg.max_active_jobs, cfg.max_inflight, cfg.policy) == (4, 2, 0)
+    assert ctypes.sizeof(binding.ServerConfig) == 32
+    h = ctypes.c_void_p()
+    cfg.policy = 7
+    assert lib.cs_ngf_server_create(ctypes.byref(cfg), ctypes.byref(h)) == binding.EINVAL
+    assert b"policy" in lib.cs_ngf_last_error()
+    cfg.policy, cfg.max_active_jobs = 1, 0
+    assert lib.cs_ngf_server_create(ctypes.byref(cfg), ctypes.byref(h)) == binding.EINVAL
+    assert h.value is None

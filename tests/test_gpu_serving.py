@@ -116,3 +116,37 @@ def test_cancel_and_injected_failure_leave_others_correct(cs):
         assert res[k]["status"] == cs.OK
         np.testing.assert_array_equal(res[k]["scores"], sc)
         np.testing.assert_array_equal(res[k]["shifts"], sh)
+
+
+@pytest.mark.parametrize("policy", ["arrival", "shortest"])
+def test_admission_policy_order(cs, policy):
+    """One active slot: a long job runs while a long and then a short job wait.
+    Arrival order admits the long one first; shortest expected work first
+    admits the short one first.  Results equal scoring each job alone."""
+    batch = 8
+    rng = np.random.default_rng(7)
+    big = synth.small_pair(301, (64, 64, 64), n_rot=2)
+    small = synth.small_pair(302, (16, 16, 16), n_rot=2)
+    q_run = synth.random_quaternions(rng, 400)
+    q_big = synth.random_quaternions(rng, 200)
+    q_small = synth.random_quaternions(rng, 8)
+    srv = cs.Server(max_active_jobs=1, max_inflight=2, batch=batch, policy=policy)
+    j_run = srv.submit(big.A, big.MA, big.B, big.MB, q_run)
+    j_big = srv.submit(big.A, big.MA, big.B, big.MB, q_big)
+    j_small = srv.submit(small.A, small.MA, small.B, small.MB, q_small)
+    r_run, r_big, r_small = (srv.wait(j, timeout_s=300) for j in (j_run, j_big, j_small))
+    srv.close()
+    assert r_run["status"] == r_big["status"] == r_small["status"] == cs.OK
+    if policy == "arrival":
+        assert r_big["queue_ms"] < r_small["queue_ms"]
+    else:
+        assert r_small["queue_ms"] < r_big["queue_ms"]
+    for p, q, r in ((big, q_big, r_big), (small, q_small, r_small)):
+        sc, sh = alone(cs, p, q, batch)
+        np.testing.assert_array_equal(r["scores"], sc)
+        np.testing.assert_array_equal(r["shifts"], sh)
+
+
+def test_unknown_policy_is_refused(cs):
+    with pytest.raises(ValueError):
+        cs.Server(policy="fastest")
