@@ -186,10 +186,14 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources the scoring kernels and their launches are built
+    from (the serving loop, search driver and allocation-free entry point are
+    left out: they launch the same kernels)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_10156_gb300", "csrc")
+    keep = ("fft_core.cuh", "kernels.cuh", "passes.cuh", "elem.cu", "cs_ngf.cu", "handle.h")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
+        if fn in keep or (fn.startswith("passes_") and fn.endswith(".cu")):
             with open(os.path.join(csrc, fn), "rb") as fh:
                 h.update(fh.read())
     return h.hexdigest()[:16]
