@@ -34,7 +34,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "150³ rotations/s (all-shift s_ANGF maps) BF16 vs FP32; p50/p99 job latency"
 UNIT = "rotations/s"
-WORKLOAD = "150^3 float32 synthetic pair, 1000 rotations, 320^3 zero-padded FFT, FP32"
+WORKLOAD = "150^3 float32 synthetic pair, 1000 rotations, FP32"
 
 
 # ------------------------------------------------------------------ inputs
@@ -155,9 +155,16 @@ def stage_bytes(dims, pad, nb, stage, nch=3, precision="fp32"):
     }.get(stage, 0)
 
 
-def zmac_flops(pad, nb, nch=3):
+PADDING = {
+    "bound": "bound-limited: per call the shortest FFT lengths that keep every shift the "
+             "Section 3.2 overlap bound admits alias-free (same scores as the full length)",
+    "full": "full linear correlation, 2n-1 per axis",
+}
+
+
+def zmac_flops(dims, pad, nb, nch=3):
     """Algorithmic flops of one z-pass launch over nb rotations: 5 L log2 L per
-    complex length-L transform (the forward input is zero past L/2, which
+    complex length-L transform (when the forward input is zero past L/2 that
     prunes the first radix-2 stage: 5 L (log2 L - 1) + L), for nch channel
     fields plus one mask field per pair of rotations over every (kx, ky)
     column, one inverse per column, and the spectral multiply-accumulate over
@@ -165,7 +172,7 @@ def zmac_flops(pad, nb, nch=3):
     Pz, Py, Px = pad
     L = Pz
     lg = math.log2(L)
-    fwd = 5 * L * (lg - 1) + L
+    fwd = 5 * L * (lg - 1) + L if 2 * dims[0] <= L else 5 * L * lg
     inv = 5 * L * lg
     cols = Px * Py
     fields = nch * nb + (nb + 1) // 2
@@ -302,8 +309,9 @@ def run_ours(args):
     R = len(quats)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     A, MA, B, MB = dev(pair["A"]), dev(pair["MA"]), dev(pair["B"]), dev(pair["MB"])
-    f = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=args.precision)
-    dims, pad = f.dims, f.pad
+    f = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=args.precision,
+                             pad_mode=args.pad_mode)
+    dims = f.dims
 
     def step():
         f.update_fixed(A, MA)
@@ -317,6 +325,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         res = step()
     torch.cuda.synchronize()
+    pad = f.pad                                     # FFT lengths the calls use
 
     def barrier():
         if ws > 1:
@@ -414,7 +423,7 @@ def run_ours(args):
 
     roofline_alu = None
     if dom == "zmac":
-        fl = sum(zmac_flops(pad, min(f.batch, R - b * f.batch)) for b in range(nbatches)) * prof_steps
+        fl = sum(zmac_flops(dims, pad, min(f.batch, R - b * f.batch)) for b in range(nbatches)) * prof_steps
         ach = fl / (stage_ms[dom] / 1000.0) / 1e12 if stage_ms[dom] > 0 else 0.0
         roofline_alu = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": ach / FP32_ALU_PEAK_TFLOPS, "kernel": dom,
@@ -438,6 +447,7 @@ def run_ours(args):
             "dtype": "f32" if args.precision == "fp32" else "f32 arithmetic, bf16 channel intermediates",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", "BF16 form"), "volume": list(dims), "fft": list(pad),
+                       "padding": PADDING[args.pad_mode], "fft_full_linear": list(f.max_pad),
                        "rotations_per_gpu": R, "batch": f.batch, "masks": "thresholded foreground",
                        "l2": "inputs larger than L2: every step streams >1 TB of FFT intermediates",
                        "step": "update_fixed + score all rotations + max over rotations"},
@@ -676,6 +686,7 @@ def main():
     ap.add_argument("--rotations", type=int, default=1000)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--precision", choices=("fp32", "bf16"), default="fp32")
+    ap.add_argument("--pad-mode", choices=("bound", "full"), default="bound")
     ap.add_argument("--ref-sample", type=int, default=16,
                     help="oracle rotations per CPU step (at most one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

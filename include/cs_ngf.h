@@ -33,7 +33,9 @@
  *     (chi_z, chi_y, chi_x), then to the smallest rotation index.
  *   - FFT lengths: per axis the smallest of {16, 32, 40, 64, 80, 100, 128,
  *     160, 200, 256, 320, 400, 512} that is >= 2n - 1 (full linear
- *     correlation), unless set.
+ *     correlation), unless set.  With bound-limited padding (the default,
+ *     cs_ngf_pad_mode) a call may use shorter lengths; the results are the
+ *     same (see cs_ngf_pad_mode).
  *
  * Memory and streams: array arguments are DEVICE pointers owned by the
  * caller unless a function says "host".  Work is enqueued on `stream` (a
@@ -75,6 +77,28 @@ typedef enum {
                        BF16 (FP32 arithmetic); the mask / overlap count path stays FP32 */
 } cs_ngf_precision;
 
+/* FFT lengths per call.  A circular correlation of length P holds at slot
+ * chi mod P the sum of the linear correlation over chi, chi - P, chi + P, ...
+ * (Eq. 7-8 evaluated with the DFT).  FULL uses P >= 2n - 1 per axis, so every
+ * shift in [-(n-1), n-1] has a slot of its own ("a suitable zero padding",
+ * Section 3.2).  BOUND uses that a shift can only be valid where the overlap
+ * bound of the mask slab counts reaches the gamma threshold (Section 3.2):
+ * N(chi) <= sum_i min(a_i, b_{i + chi}) along each axis, a the slab counts of
+ * M_A and b those of the rotated mask.  Each scoring call first counts the
+ * rotated masks of all its rotations, takes the range [lo, hi] of shifts the
+ * bound admits over all of them, and uses per axis the shortest supported
+ * length P >= n + max(-lo, hi).  Then for every admitted shift chi the other
+ * shifts chi + kP, k != 0, fall outside [-(n-1), n-1] where the linear
+ * correlation lives, so its slot holds exactly its own value; shifts outside
+ * the range are invalid and reported as such, as with FULL.  Scores agree
+ * with FULL up to FP32 rounding.  The call synchronises its stream once to
+ * read the range, and recomputes the fixed spectra (about the cost of one
+ * rotation) when the length changes. */
+typedef enum {
+  CS_NGF_PAD_FULL = 0,  /* P >= 2n - 1 on every call */
+  CS_NGF_PAD_BOUND = 1  /* per call, the shortest length the shift bound allows (default) */
+} cs_ngf_pad_mode;
+
 typedef struct {
   float eps;         /* Eq. 1 regulariser; the paper uses 1e-5 */
   float gamma;       /* minimum overlap fraction in (0, 1]; the paper uses 0.5 */
@@ -87,19 +111,23 @@ typedef struct {
                         scores in the last bit */
   int32_t measure;   /* cs_ngf_measure; default CS_NGF_SQUARED */
   int32_t precision; /* cs_ngf_precision; default CS_NGF_FP32 */
+  int32_t pad_mode;  /* cs_ngf_pad_mode; cs_ngf_default_config sets CS_NGF_PAD_BOUND.  The
+                        lengths from pad (or automatic) are then the largest a call uses */
 } cs_ngf_config;
 
 typedef struct {
   int32_t dims[3];              /* nz, ny, nx */
-  int32_t pad[3];               /* FFT lengths in use */
+  int32_t pad[3];               /* FFT lengths in use (those of the last call) */
   int32_t batch;                /* rotations per launch group */
   int64_t sum_mask_a;           /* sum of M_A */
   int64_t fixed_bytes;          /* device bytes of the fixed spectra */
   int64_t workspace_bytes;      /* device bytes of the per-batch workspace */
+  int32_t max_pad[3];           /* largest FFT lengths (buffers are sized for them) */
+  int32_t pad_mode;             /* cs_ngf_pad_mode */
 } cs_ngf_info;
 
 /* Fill *cfg with the paper's settings (eps 1e-5, gamma 0.5, automatic pad and
- * batch). */
+ * batch) and bound-limited padding. */
 void cs_ngf_default_config(cs_ngf_config* cfg);
 
 /* Section 3.1, Eq. 1, 6-8, A side: the NGF of the fixed volume A, its six
@@ -123,8 +151,9 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
  *   best_score  device float32 [R]; -inf where a rotation has no valid shift
  *   best_shift  device int32 [R][3] (chi_z, chi_y, chi_x); 0 where no valid shift
  * Asynchronous on `stream` except for the small host-to-device upload of the
- * rotation matrices, which is staged through the handle (the call returns
- * once its work is enqueued).  Errors: EINVAL, ECUDA. */
+ * rotation matrices, which is staged through the handle, and, with
+ * bound-limited padding, one wait for the shift range of the call (the call
+ * returns once the scoring work is enqueued).  Errors: EINVAL, ECUDA. */
 cs_ngf_status cs_ngf_score_rotations(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
                                      const double* quats, int32_t R, float* best_score,
                                      int32_t* best_shift, void* stream);

@@ -42,17 +42,19 @@ STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "othe
 class Config(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32), ("measure", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("pad_mode", ctypes.c_int32)]
 
 
 MEASURES = {"squared": 0, "unsquared": 1}
 PRECISIONS = {"fp32": 0, "bf16": 1}
+PAD_MODES = {"full": 0, "bound": 1}
 
 
 class Info(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("pad", ctypes.c_int32 * 3),
                 ("batch", ctypes.c_int32), ("sum_mask_a", ctypes.c_int64),
-                ("fixed_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+                ("fixed_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("max_pad", ctypes.c_int32 * 3), ("pad_mode", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -189,7 +191,7 @@ class Fixed:
     """Handle on the device-resident fixed-volume spectra (cs_ngf_prepare_fixed)."""
 
     def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None,
-                 measure="squared", precision="fp32"):
+                 measure="squared", precision="fp32", pad_mode="bound"):
         import torch
         if A.dim() != 3:
             raise ValueError("A must be [nz][ny][nx]")
@@ -206,8 +208,10 @@ class Fixed:
         cfg.batch = int(batch)
         cfg.measure = MEASURES[measure]
         cfg.precision = PRECISIONS[precision]
+        cfg.pad_mode = PAD_MODES[pad_mode]
         self.measure = measure
         self.precision = precision
+        self.pad_mode = pad_mode
         dims = (ctypes.c_int32 * 3)(*self.dims)
         h = ctypes.c_void_p()
         st = _check(_lib.cs_ngf_prepare_fixed(_dev_ptr(A, torch.float32, "A"),
@@ -216,13 +220,23 @@ class Fixed:
                                               ctypes.byref(h)), "cs_ngf_prepare_fixed")
         self._h = h
         self._keep = (A, MA)
-        info = Info()
-        _check(_lib.cs_ngf_get_info(self._h, ctypes.byref(info)), "cs_ngf_get_info")
-        self.pad = tuple(info.pad)
+        info = self._info()
+        self.max_pad = tuple(info.max_pad)
         self.batch = int(info.batch)
         self.sum_mask_a = int(info.sum_mask_a)
         self.fixed_bytes = int(info.fixed_bytes)
         self.workspace_bytes = int(info.workspace_bytes)
+
+    def _info(self):
+        info = Info()
+        _check(_lib.cs_ngf_get_info(self._h, ctypes.byref(info)), "cs_ngf_get_info")
+        return info
+
+    @property
+    def pad(self):
+        """FFT lengths (z, y, x) in use: those of the last call (bound-limited
+        padding may shorten them below max_pad)."""
+        return tuple(self._info().pad)
 
     @property
     def handle(self):
@@ -393,7 +407,7 @@ class Server:
         self._R = {}
 
     def submit(self, A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, batch=0,
-               measure="squared", precision="fp32") -> int:
+               measure="squared", precision="fp32", pad_mode="bound") -> int:
         arrs = []
         for name, a, dt in (("A", A, np.float32), ("maskA", MA, np.uint8), ("B", B, np.float32),
                             ("maskB", MB, np.uint8)):
@@ -407,6 +421,7 @@ class Server:
         cfg.eps, cfg.gamma, cfg.batch = float(eps), float(gamma), int(batch)
         cfg.measure = MEASURES[measure]
         cfg.precision = PRECISIONS[precision]
+        cfg.pad_mode = PAD_MODES[pad_mode]
         if pad is not None:
             for i, p in enumerate(pad):
                 cfg.pad[i] = int(p)
@@ -458,7 +473,7 @@ class Server:
 
 
 def global_align(A, MA, B, MB, schedule=None, seed=0x5EED, start=(0.0, 0.0, 0.0), eps=1e-5,
-                 gamma=0.5, measure="squared", stream=None):
+                 gamma=0.5, measure="squared", stream=None, pad_mode="bound"):
     """Pyramid random search of Section 3.2 (cs_ngf_global_align) on device
     volumes.  schedule: list of (sigma, d, u_deg, a, p) per level, p being the
     number of starting points of that level (the first level's p is 1); None
@@ -480,6 +495,7 @@ def global_align(A, MA, B, MB, schedule=None, seed=0x5EED, start=(0.0, 0.0, 0.0)
     cfg = Config()
     _lib.cs_ngf_default_config(ctypes.byref(cfg))
     cfg.eps, cfg.gamma, cfg.measure = float(eps), float(gamma), MEASURES[measure]
+    cfg.pad_mode = PAD_MODES[pad_mode]
     dims = (ctypes.c_int32 * 3)(*tuple(A.shape))
     res = SearchResult()
     _check(_lib.cs_ngf_global_align(_dev_ptr(A, torch.float32, "A"), _dev_ptr(MA, torch.uint8, "maskA"),

@@ -190,17 +190,22 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->stage_M);
   cudaFree(f->res_score);
   cudaFree(f->res_shift);
+  cudaFree(f->A_keep);
+  cudaFree(f->MA_keep);
+  cudaFree(f->ubound);
+  cudaFreeHost(f->ubound_h);
   delete f;
 }
 
-cs_ngf_status make_twiddles(int P, float2** out) {
+// twiddle table exp(-2 pi i m / P), m < P, into dst (at least P entries);
+// synchronous, so no kernel may still read dst
+cs_ngf_status fill_twiddles(int P, float2* dst) {
   std::vector<float2> h(P);
   for (int m = 0; m < P; ++m) {
     h[m].x = (float)ctw::cos2pi(m, P);
     h[m].y = (float)(-ctw::sin2pi(m, P));
   }
-  CS_CUDA(dalloc(out, (size_t)P));
-  CS_CUDA(cudaMemcpy(*out, h.data(), sizeof(float2) * P, cudaMemcpyHostToDevice));
+  CS_CUDA(cudaMemcpy(dst, h.data(), sizeof(float2) * P, cudaMemcpyHostToDevice));
   return CS_NGF_OK;
 }
 
@@ -365,6 +370,70 @@ cs_ngf_status run_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* MA, cuda
   return CS_NGF_OK;
 }
 
+// switch the handle to FFT lengths pad (each <= alloc_pad): twiddles, fixed
+// spectra at the new lengths, and a new graph on the next full launch group
+cs_ngf_status set_pads(cs_ngf_fixed* f, const int pad[3], cudaStream_t st) {
+  Geo& g = f->g;
+  const int cur[3] = {g.Pz, g.Py, g.Px};
+  if (cur[0] == pad[0] && cur[1] == pad[1] && cur[2] == pad[2]) return CS_NGF_OK;
+  CS_CUDA(cudaStreamSynchronize(st));            // nothing may still read the old tables
+  for (int a = 0; a < 3; ++a)
+    if (cur[a] != pad[a])
+      if (cs_ngf_status s = fill_twiddles(pad[a], f->tw[a])) return s;
+  g.Pz = pad[0];
+  g.Py = pad[1];
+  g.Px = pad[2];
+  if (f->gexec) {                                // the captured launches hold the old lengths
+    cudaGraphExecDestroy(f->gexec);
+    f->gexec = nullptr;
+  }
+  return run_fixed(f, f->A_keep, f->MA_keep, st);
+}
+
+// Section 3.2 minimum overlap -> FFT lengths: the union over the R uploaded
+// rotations of the slab-bound shift ranges (the same counts and bound the
+// launch groups compute), then per axis the shortest supported length
+// P >= n + max(-chi_lo, chi_hi), at most alloc_pad
+cs_ngf_status bound_pads_impl(cs_ngf_fixed* f, int R, cudaStream_t st) {
+  if (f->pad_mode != CS_NGF_PAD_BOUND) return CS_NGF_OK;
+  const Geo& g = f->g;
+  const size_t nmarg = (size_t)g.nz + g.ny + g.nx;
+  { Stage sp(f, 7, st); k_bound_reset<<<1, 32, 0, st>>>(f->ubound); }
+  if (cs_ngf_status s = check_launch("bound reset")) return s;
+  for (int r0 = 0; r0 < R; r0 += f->batch) {
+    const int nb = std::min(f->batch, R - r0);
+    CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int) * nb, st));
+    CS_CUDA(cudaMemsetAsync(f->margB, 0, sizeof(int) * nmarg * nb, st));
+    {
+      Stage sp(f, 0, st);
+      k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, f->rot_d + r0, g, nullptr, nullptr,
+                                                       f->msum, f->margB);
+    }
+    if (cs_ngf_status s = check_launch("mask counts")) return s;
+    {
+      Stage sp(f, 7, st);
+      k_shift_bounds<<<dim3((unsigned)nb, 3u), 512, 0, st>>>(f->margA, f->margB, f->msum, f->sumA,
+                                                             f->gamma, g, f->bounds);
+    }
+    if (cs_ngf_status s = check_launch("shift bounds")) return s;
+    { Stage sp(f, 7, st); k_bound_union<<<(nb + 127) / 128, 128, 0, st>>>(f->bounds, nb, f->ubound); }
+    if (cs_ngf_status s = check_launch("bound union")) return s;
+  }
+  CS_CUDA(cudaMemcpyAsync(f->ubound_h, f->ubound, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaStreamSynchronize(st));
+  const int dims[3] = {g.nz, g.ny, g.nx};
+  int pad[3];
+  for (int a = 0; a < 3; ++a) {
+    const int n = dims[a], lo = f->ubound_h[2 * a], hi = f->ubound_h[2 * a + 1];
+    // no rotation admits a shift: any length >= n gives the same (empty) result
+    const int need = lo > hi ? n : n + std::max(n - 1 - lo, hi - (n - 1));
+    pad[a] = f->alloc_pad[a];
+    for (int v : kPads)
+      if (v >= need) { pad[a] = std::min(v, f->alloc_pad[a]); break; }
+  }
+  return set_pads(f, pad, st);
+}
+
 cs_ngf_status check_volume_args(const cs_ngf_fixed* f, const float* B, const uint8_t* MB) {
   if (!f) return fail(CS_NGF_EINVAL, "handle is NULL");
   if (!B || !MB) return fail(CS_NGF_EINVAL, "B or maskB is NULL");
@@ -399,6 +468,7 @@ cs_ngf_status score_all(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cons
   if (!best_score || !best_shift) return fail(CS_NGF_EINVAL, "output pointer is NULL");
   if (cs_ngf_status s = upload_rotations(f, quats, R, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, MB, st)) return s;
+  if (cs_ngf_status s = bound_pads_impl(f, R, st)) return s;
   return score_range_impl(f, 0, R, best_score, best_shift, st);
 }
 
@@ -413,6 +483,8 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
     return fail(CS_NGF_EINVAL, "unknown measure");
   if (cfg.precision != CS_NGF_FP32 && cfg.precision != CS_NGF_BF16)
     return fail(CS_NGF_EINVAL, "unknown precision");
+  if (cfg.pad_mode != CS_NGF_PAD_FULL && cfg.pad_mode != CS_NGF_PAD_BOUND)
+    return fail(CS_NGF_EINVAL, "unknown pad_mode");
   for (int a = 0; a < 3; ++a) {
     pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
     if (!pad_supported(pad[a]))
@@ -477,6 +549,9 @@ cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int
                           cudaStream_t st) {
   return ::score_range_impl(f, r0, n, best_score, best_shift, st);
 }
+cs_ngf_status bound_pads(cs_ngf_fixed* f, int R, cudaStream_t st) {
+  return ::bound_pads_impl(f, R, st);
+}
 cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
   return ::resolve_pads_impl(dims, cfg, pad);
 }
@@ -485,7 +560,8 @@ size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int meas
   size_t tw = 0;
   for (int a = 0; a < 3; ++a) tw += (size_t)pad[a] * sizeof(float2);
   const size_t nmarg = (size_t)dims[0] + dims[1] + dims[2];
-  return z.uv_elems * sizeof(float2) + (size_t)batch * z.per_rot + z.shared_ws +
+  const size_t keep = (size_t)dims[0] * dims[1] * dims[2] * 5;    // A, M_A copies (bound-limited padding)
+  return z.uv_elems * sizeof(float2) + keep + (size_t)batch * z.per_rot + z.shared_ws +
          (size_t)batch * (sizeof(int) + sizeof(float) + sizeof(unsigned long long) + 6 * sizeof(int)) +
          (size_t)(batch + 1) * nmarg * sizeof(int) + tw;
 }
@@ -500,6 +576,7 @@ void cs_ngf_default_config(cs_ngf_config* cfg) {
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->eps = 1e-5f;
   cfg->gamma = 0.5f;
+  cfg->pad_mode = CS_NGF_PAD_BOUND;
 }
 
 int32_t cs_ngf_auto_pad(int32_t n) { return (n >= 2 && n <= 256) ? auto_pad(n) : 0; }
@@ -546,6 +623,8 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   g.nch = channel_fields(cfg.measure);
   g.nf = g.nch + 1;
   g.bf16 = cfg.precision == CS_NGF_BF16 ? 1 : 0;
+  for (int a = 0; a < 3; ++a) f->alloc_pad[a] = pad[a];
+  f->pad_mode = cfg.pad_mode;
 
   const Sizes sz = sizes_for(dims, pad, cfg.measure, cfg.precision);
   f->f02_elems = sz.f02_elems;
@@ -584,11 +663,18 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->keys, (size_t)batch));
   f->fixed_bytes = uv_elems * sizeof(float2);
   f->workspace_bytes = (size_t)batch * per_rot + shared_ws;
-  for (int a = 0; a < 3; ++a) {
-    f->tw[a] = nullptr;
-    for (int b = 0; b < a; ++b)
-      if (pad[b] == pad[a]) f->tw[a] = f->tw[b];
-    if (!f->tw[a]) CS_TRY(make_twiddles(pad[a], &f->tw[a]));
+  for (int a = 0; a < 3; ++a) {                 // one table per axis: the lengths may part
+    CS_TRYC(dalloc(&f->tw[a], (size_t)pad[a]));
+    CS_TRY(fill_twiddles(pad[a], f->tw[a]));
+  }
+  if (f->pad_mode == CS_NGF_PAD_BOUND) {
+    CS_TRYC(dalloc(&f->A_keep, (size_t)g.nvox));
+    CS_TRYC(dalloc(&f->MA_keep, (size_t)g.nvox));
+    CS_TRYC(dalloc(&f->ubound, (size_t)6));
+    CS_TRYC(cudaMallocHost((void**)&f->ubound_h, 6 * sizeof(int)));
+    CS_TRYC(cudaMemcpyAsync(f->A_keep, A, sizeof(float) * g.nvox, cudaMemcpyDeviceToDevice, st));
+    CS_TRYC(cudaMemcpyAsync(f->MA_keep, maskA, (size_t)g.nvox, cudaMemcpyDeviceToDevice, st));
+    f->fixed_bytes += (size_t)g.nvox * 5;
   }
 
   // A side into the new handle
@@ -673,6 +759,7 @@ cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* m
   if (cs_ngf_status s = ensure_results(f, 1)) return s;
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
+  if (cs_ngf_status s = bound_pads_impl(f, 1, st)) return s;
   return score_batch(f, 0, 1, f->res_score, f->res_shift, map, st);
 }
 
@@ -699,6 +786,8 @@ cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info) {
   info->sum_mask_a = f->sumA;
   info->fixed_bytes = (int64_t)f->fixed_bytes;
   info->workspace_bytes = (int64_t)f->workspace_bytes;
+  for (int a = 0; a < 3; ++a) info->max_pad[a] = f->alloc_pad[a];
+  info->pad_mode = f->pad_mode;
   return CS_NGF_OK;
 }
 
@@ -709,7 +798,12 @@ cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t
   if (!f) return fail(CS_NGF_EINVAL, "handle is NULL");
   if (!A || !maskA) return fail(CS_NGF_EINVAL, "A or maskA is NULL");
   DeviceGuard guard(f->device);
-  return run_fixed(f, A, maskA, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (f->A_keep) {                               // kept for later changes of FFT length
+    CS_CUDA(cudaMemcpyAsync(f->A_keep, A, sizeof(float) * f->g.nvox, cudaMemcpyDeviceToDevice, st));
+    CS_CUDA(cudaMemcpyAsync(f->MA_keep, maskA, (size_t)f->g.nvox, cudaMemcpyDeviceToDevice, st));
+  }
+  return run_fixed(f, A, maskA, st);
 }
 
 cs_ngf_status cs_ngf_set_profiling(cs_ngf_fixed* f, int32_t on) {

@@ -112,9 +112,11 @@ k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
       float val;
       uint8_t m;
       resample_voxel(BM, R, g, x, y, z, val, m);
-      const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
-      Bh[idx] = val;
-      Mh[idx] = m;
+      if (Bh) {                                // NULL: mask counts only (bounds pre-pass)
+        const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
+        Bh[idx] = val;
+        Mh[idx] = m;
+      }
       mk = m;
     }
     c += mk;
@@ -197,6 +199,22 @@ __global__ void k_shift_bounds(const int* __restrict__ margA, const int* __restr
   if (threadIdx.x == 0) {
     bounds[r * 6 + 2 * a] = lo_s;
     bounds[r * 6 + 2 * a + 1] = hi_s;
+  }
+}
+
+__global__ void k_bound_reset(int* __restrict__ u) {
+  if (threadIdx.x < 6) u[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
+}
+
+__global__ void k_bound_union(const int* __restrict__ bounds, int nrot, int* __restrict__ u) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrot; r += gridDim.x * blockDim.x) {
+    const int* b = bounds + 6 * r;
+    if (b[0] > b[1] || b[2] > b[3] || b[4] > b[5]) continue;   // no shift can be valid
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&u[2 * a], b[2 * a]);
+      atomicMax(&u[2 * a + 1], b[2 * a + 1]);
+    }
   }
 }
 

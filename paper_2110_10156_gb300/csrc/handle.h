@@ -18,6 +18,15 @@ struct cs_ngf_fixed {
   float eps = 1e-5f, gamma = 0.5f;
   int batch = 1;
   int sumA = 0;
+  // FFT lengths the buffers are sized for (the automatic or requested ones);
+  // g.Pz/Py/Px are the lengths in use, which bound-limited padding
+  // (pad_mode CS_NGF_PAD_BOUND) lowers per call
+  int alloc_pad[3] = {0, 0, 0};
+  int pad_mode = 0;
+  float* A_keep = nullptr;     // copies of A and M_A: the fixed spectra are
+  uint8_t* MA_keep = nullptr;  // recomputed when the lengths in use change
+  int* ubound = nullptr;       // device: union of a call's shift bounds [6]
+  int* ubound_h = nullptr;     // pinned host copy of it
   size_t f02_elems = 0, f13_elems = 0;
   float2* UV = nullptr;
   float* Bh = nullptr;
@@ -66,6 +75,12 @@ cs_ngf_status fail(cs_ngf_status s, const std::string& msg);
 cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* quats, int R, cudaStream_t st);
 // (B, M_B) -> f->BM for the following score calls
 cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st);
+// bound-limited padding: for the R uploaded rotations (B already packed),
+// bound the shifts that can be valid, pick per axis the shortest supported
+// FFT length that keeps all of them alias-free (at most alloc_pad) and switch
+// the handle to it (fixed spectra recomputed when it changes).  Synchronises
+// `st` once.  A no-op unless pad_mode is CS_NGF_PAD_BOUND.
+cs_ngf_status bound_pads(cs_ngf_fixed* f, int R, cudaStream_t st);
 // score rotations [r0, r0 + n) of the uploaded set into best_score / best_shift
 // (device, indexed from r0), in launch groups of f->batch
 cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int32_t* best_shift,

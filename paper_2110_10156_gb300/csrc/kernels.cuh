@@ -90,6 +90,8 @@ __device__ __forceinline__ unsigned long long make_key(float s, unsigned lin) {
 // read as (value, mask) pairs prepared by k_pack_bm.
 __global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict__ MB, long long n,
                           float2* __restrict__ BM);
+// With Bh == NULL it writes no volumes and only counts the rotated masks
+// (msum, marg): the pre-pass that bounds the shifts of a whole call.
 __global__ void k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
                            float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
                            int* __restrict__ marg);
@@ -111,6 +113,11 @@ __global__ void k_shift_bounds(const int* __restrict__ margA, const int* __restr
                                const int* __restrict__ msumB, int sumA, float gamma, Geo g,
                                int* __restrict__ bounds);
 __global__ void k_fill(float* __restrict__ p, long long n, float v);
+// Union of the shift bounds of nrot rotations into u[6] = {lo_z, hi_z, lo_y,
+// hi_y, lo_x, hi_x} (slots v = chi + n - 1), over the rotations for which some
+// shift can be valid; k_bound_reset sets u to the empty range first.
+__global__ void k_bound_reset(int* __restrict__ u);
+__global__ void k_bound_union(const int* __restrict__ bounds, int nrot, int* __restrict__ u);
 
 // sum of a uint8 mask (for the fixed volume)
 __global__ void k_mask_sum(const uint8_t* __restrict__ M, long long n, int* __restrict__ out);

@@ -6,12 +6,34 @@
 
 namespace csngf {
 
-// output index m of a length-P transform -> shift slot v = chi + n - 1, or -1
-__device__ __forceinline__ int shift_slot(int m, int n, int P) {
-  if (m <= n - 1) return m + n - 1;
-  if (m >= P - (n - 1)) return m - P + n - 1;
+// Output index m of a length-P circular correlation -> the shift slot
+// v = chi + n - 1 in [lo, hi] with chi = m or chi = m - P, or -1 if neither
+// lies there.  Slot m sums the linear correlation at every chi = m (mod P);
+// it equals the value at the one chi in [lo, hi] when every other chi of that
+// class lies outside the linear support [-(n-1), n-1], which the caller
+// guarantees by P >= n + max(n-1-lo, hi-(n-1)) (with lo = 0, hi = 2n-2 that
+// is the full linear-correlation length P >= 2n-1).
+__device__ __forceinline__ int shift_slot(int m, int n, int P, int lo, int hi) {
+  const int v1 = m + n - 1;                      // chi = m
+  if (m <= n - 1 && v1 >= lo && v1 <= hi) return v1;
+  const int v2 = m - P + n - 1;                  // chi = m - P
+  if (v2 >= 0 && v2 >= lo && v2 <= hi) return v2;
   return -1;
 }
+
+// Forward-transform inputs: a volume side n is zero padded to P.  When
+// n <= P/2 the upper half of every step-1 sequence is zero and step 1 is the
+// pruned form (FourStep::step1_half); otherwise all N1 inputs are read.
+template <class FS, bool HALF>
+struct FwdIn {
+  static constexpr int NI = HALF ? FS::N1 / 2 : FS::N1;   // step-1 inputs per thread
+  template <int S, bool TS = false>
+  __device__ __forceinline__ static void step1(float2 (&v)[NI], float2* ex_seq, int n2,
+                                               const float2* __restrict__ twN) {
+    if constexpr (HALF) FS::template step1_half<S, TS>(v, ex_seq, n2, twN);
+    else FS::template step1<S, TS>(v, ex_seq, n2, twN);
+  }
+};
 
 template <class K>
 static void set_smem(K kern, size_t bytes) {
@@ -24,12 +46,25 @@ static void set_smem(K kern, size_t bytes) {
 // complex fields, and the x-axis FFT of every row (zero padded to Px).
 // Block: ROWS rows of one slab; thread (row, n2) gathers x = N2*n1 + n2.
 // ---------------------------------------------------------------------------
-template <int P, int ROWS, bool BF>
+// A thread keeps the NGF (x, y, z, mask) of its step-1 inputs across the
+// four fields: in registers for half-length inputs, in its own slots of
+// shared memory [NI][NT] (float4) for full-length ones, which would spill.
+template <int P, bool HALF>
+struct FwdXCfg {
+  static constexpr int ROWS = (256 / Split<P>::N2) > 0 ? (256 / Split<P>::N2) : 1;
+  static constexpr int NT = ROWS * Split<P>::N2;
+  static constexpr int NI = FwdIn<FourStep<P>, HALF>::NI;
+  static constexpr size_t ex_bytes = ((size_t)ROWS * FourStep<P>::CS * sizeof(float2) + 15) / 16 * 16;
+  static constexpr size_t smem_bytes = ex_bytes + (HALF ? 0 : (size_t)NI * NT * sizeof(float4));
+};
+
+template <int P, int ROWS, bool BF, bool HALF>
 __global__ void __launch_bounds__(ROWS * Split<P>::N2, 2)
 k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __restrict__ F0,
         const float2* __restrict__ tw, Geo g, long long nrows) {
   using FS = FourStep<P>;
-  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
+  using FI = FwdIn<FS, HALF>;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FI::NI;
   extern __shared__ float2 ex[];
   const int t = threadIdx.x;
   const int lrow = t / N2, n2 = t - lrow * N2;
@@ -39,8 +74,12 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
   const int y = row_ok ? (int)(grow - rz * g.ny) : 0;
   const int r = (int)(rz / g.nz), z = (int)(rz - (long long)r * g.nz);
 
-  // x = N2*n1 + n2 < nx <= P/2 only for n1 < N1/2: the upper half is zero
-  float vx[H], vy[H], vz[H], mm[H];
+  // x = N2*n1 + n2 < nx: with nx <= P/2 only n1 < N1/2 can hold data
+  constexpr bool NS = !HALF;                  // NGF staged in shared memory
+  constexpr int HR = NS ? 1 : H;
+  float vx[HR], vy[HR], vz[HR], mm[HR];
+  float4* ngs = reinterpret_cast<float4*>(reinterpret_cast<char*>(ex) + FwdXCfg<P, HALF>::ex_bytes);
+  const int NTX = ROWS * N2;
   const float* V = Bh + (long long)r * g.nvox;
   const uint8_t* M = Mh + (long long)r * g.nvox;
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
@@ -50,7 +89,7 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
 #pragma unroll
   for (int n1 = 0; n1 < H; ++n1) {
     const int x = N2 * n1 + n2;
-    vx[n1] = vy[n1] = vz[n1] = mm[n1] = 0.0f;
+    float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (row_ok && x < g.nx) {
       const int xm = max(x - 1, 0), xp = min(x + 1, g.nx - 1);
       const float gx = 0.5f * (__ldg(&V[base + xp]) - __ldg(&V[base + xm]));
@@ -59,10 +98,15 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
       const float gz = 0.5f * (__ldg(&V[(long long)zp * sz + (long long)y * sy + x]) -
                                __ldg(&V[(long long)zm * sz + (long long)y * sy + x]));
       const float inv = rsqrtf(gx * gx + gy * gy + gz * gz + g.eps2);
-      vx[n1] = gx * inv;
-      vy[n1] = gy * inv;
-      vz[n1] = gz * inv;
-      mm[n1] = M[base + x] ? 1.0f : 0.0f;
+      q = make_float4(gx * inv, gy * inv, gz * inv, M[base + x] ? 1.0f : 0.0f);
+    }
+    if constexpr (NS) {
+      ngs[n1 * NTX + t] = q;
+    } else {
+      vx[n1] = q.x;
+      vy[n1] = q.y;
+      vz[n1] = q.z;
+      mm[n1] = q.w;
     }
   }
   const long long rows_per_field = (long long)g.nz * g.ny;
@@ -82,13 +126,20 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
     float2 v[H];
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) {
-      const float m = mm[n1];
+      float X, Y, Z, m;
+      if constexpr (NS) {
+        const float4 q = ngs[n1 * NTX + t];     // this thread's own slot
+        X = q.x; Y = q.y; Z = q.z; m = q.w;
+      } else {
+        X = vx[n1 < HR ? n1 : 0]; Y = vy[n1 < HR ? n1 : 0]; Z = vz[n1 < HR ? n1 : 0];
+        m = mm[n1 < HR ? n1 : 0];
+      }
       switch (code) {
-        case 0: v[n1] = make_float2(m * vx[n1] * vx[n1], m * vy[n1] * vy[n1]); break;
-        case 1: v[n1] = make_float2(m * vz[n1] * vz[n1], m * vx[n1] * vy[n1]); break;
-        case 2: v[n1] = make_float2(m * vx[n1] * vz[n1], m * vy[n1] * vz[n1]); break;
-        case 4: v[n1] = make_float2(m * vx[n1], m * vy[n1]); break;
-        case 5: v[n1] = make_float2(m * vz[n1], 0.0f); break;
+        case 0: v[n1] = make_float2(m * X * X, m * Y * Y); break;
+        case 1: v[n1] = make_float2(m * Z * Z, m * X * Y); break;
+        case 2: v[n1] = make_float2(m * X * Z, m * Y * Z); break;
+        case 4: v[n1] = make_float2(m * X, m * Y); break;
+        case 5: v[n1] = make_float2(m * Z, 0.0f); break;
         default: {
           const int x = N2 * n1 + n2;
           float m2 = 0.0f;
@@ -98,7 +149,7 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
         }
       }
     }
-    FS::template step1_half<-1>(v, ex + lrow * CS, n2, tw);
+    FI::template step1<-1>(v, ex + lrow * CS, n2, tw);
     __syncthreads();
     if (t < ROWS * N1) {
       const int lr = t / N1, k1 = t - lr * N1;
@@ -125,21 +176,27 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
   }
 }
 
+template <int P, bool HALF>
+void launch_fwd_x_t(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw, Geo g, int nrot,
+                    cudaStream_t st) {
+  constexpr int N2 = Split<P>::N2;
+  constexpr int ROWS = FwdXCfg<P, HALF>::ROWS;
+  const long long nrows = (long long)nrot * g.nz * g.ny;
+  const size_t smem = FwdXCfg<P, HALF>::smem_bytes;
+  const unsigned blocks = (unsigned)((nrows + ROWS - 1) / ROWS);
+  auto go = [&](auto kern) {
+    set_smem(kern, smem);
+    kern<<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
+  };
+  if (g.bf16) go(k_fwd_x<P, ROWS, true, HALF>);
+  else go(k_fwd_x<P, ROWS, false, HALF>);
+}
+
 template <int P>
 void launch_fwd_x(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw, Geo g, int nrot,
                   cudaStream_t st) {
-  constexpr int N2 = Split<P>::N2;
-  constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
-  const long long nrows = (long long)nrot * g.nz * g.ny;
-  const size_t smem = (size_t)ROWS * FourStep<P>::CS * sizeof(float2);
-  const unsigned blocks = (unsigned)((nrows + ROWS - 1) / ROWS);
-  if (g.bf16) {
-    set_smem(k_fwd_x<P, ROWS, true>, smem);
-    k_fwd_x<P, ROWS, true><<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
-  } else {
-    set_smem(k_fwd_x<P, ROWS, false>, smem);
-    k_fwd_x<P, ROWS, false><<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
-  }
+  if (2 * g.nx <= P) launch_fwd_x_t<P, true>(Bh, Mh, F0, tw, g, nrot, st);
+  else launch_fwd_x_t<P, false>(Bh, Mh, F0, tw, g, nrot, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -167,11 +224,12 @@ template <int P> struct FwdYCfg {
   static constexpr int MIN_BLOCKS = pass_blocks(NT, smem_bytes, Split<P>::N2 > 20 ? 80 : 48);
 };
 
-template <int P, int W, bool BF>
+template <int P, int W, bool BF, bool HALF>
 __global__ void __launch_bounds__(W * Split<P>::N2, FwdYCfg<P>::MIN_BLOCKS)
 k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __restrict__ tw,
         Geo g) {
   using FS = FourStep<P>;
+  using FI = FwdIn<FS, HALF>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
   extern __shared__ float2 ex[];
   const int t = threadIdx.x;
@@ -187,23 +245,23 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
     const int kx = kx0 + col;
     const char* src = Fields<BF>::field(F0, g, (long long)g.nz * g.ny * g.Px, r, j);
     const long long zoff = (long long)z * g.ny * g.Px;
-    float2 v[FS::H];                      // y < ny <= P/2: upper half is zero
+    float2 v[FI::NI];                     // y < ny: with ny <= P/2 the upper half is zero
     if (is_mask) {
 #pragma unroll
-      for (int n1 = 0; n1 < FS::H; ++n1) {
+      for (int n1 = 0; n1 < FI::NI; ++n1) {
         const int y = N2 * n1 + n2;
         v[n1] = (y < g.ny && kx < g.Px) ? Fields<BF>::get(src, zoff + (long long)y * g.Px + kx, true)
                                         : make_float2(0.f, 0.f);
       }
     } else {
 #pragma unroll
-      for (int n1 = 0; n1 < FS::H; ++n1) {
+      for (int n1 = 0; n1 < FI::NI; ++n1) {
         const int y = N2 * n1 + n2;
         v[n1] = (y < g.ny && kx < g.Px) ? Fields<BF>::get(src, zoff + (long long)y * g.Px + kx, false)
                                         : make_float2(0.f, 0.f);
       }
     }
-    FS::template step1_half<-1>(v, ex + col * CS, n2, tw);
+    FI::template step1<-1>(v, ex + col * CS, n2, tw);
   }
   __syncthreads();
   if (t < W * N1) {
@@ -230,13 +288,13 @@ void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, c
   constexpr int W = FwdYCfg<P>::W, N2 = Split<P>::N2;
   const size_t smem = FwdYCfg<P>::smem_bytes;
   dim3 grid((unsigned)(nrot * g.nf * g.nz), (unsigned)((g.Px + W - 1) / W));
-  if (g.bf16) {
-    set_smem(k_fwd_y<P, W, true>, smem);
-    k_fwd_y<P, W, true><<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
-  } else {
-    set_smem(k_fwd_y<P, W, false>, smem);
-    k_fwd_y<P, W, false><<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
-  }
+  auto go = [&](auto kern) {
+    set_smem(kern, smem);
+    kern<<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
+  };
+  const bool half = 2 * g.ny <= P;
+  if (g.bf16) half ? go(k_fwd_y<P, W, true, true>) : go(k_fwd_y<P, W, true, false>);
+  else half ? go(k_fwd_y<P, W, false, true>) : go(k_fwd_y<P, W, false, false>);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,20 +306,32 @@ void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, c
 // keeping the 2nz-1 shift planes.  Loops over the batch's rotations so the
 // fixed spectra tile stays in L2.
 // ---------------------------------------------------------------------------
-template <int P>
+// shared memory of a zmac block with W primary columns (see ZmacCfg)
+template <int P, bool HALF>
+constexpr size_t zmac_smem_base(int W) {
+  const int NI = HALF ? Split<P>::N1 / 2 : Split<P>::N1;
+  const size_t cs = 2 * W < 16 ? FourStep<P, true>::CS : FourStep<P, false>::CS;
+  return ((size_t)7 * W * P + (size_t)2 * W * cs + (size_t)2 * NI * (2 * W * Split<P>::N2)) *
+         sizeof(float2);
+}
+
+template <int P, bool HALF>
 struct ZmacCfg {
   // primary columns per block: the block's tile of the seven fixed spectra
-  // (7 * W * P complex values) stays in shared memory for the whole batch
-  static constexpr int W = P <= 320 ? 8 : 4;
+  // (7 * W * P complex values) stays in shared memory for the whole batch;
+  // 8 columns where the tile, the exchange and two input stages fit (at most
+  // 227 KB per block), else 4
+  static constexpr int W =
+      (P <= 320 && zmac_smem_base<P, HALF>(8) + P * sizeof(float2) <= 232448) ? 8 : 4;
   static constexpr int NT = 2 * W * Split<P>::N2;
   // exchange rows unpadded when 16 columns fill a half-warp (natural order)
   static constexpr bool PAD = 2 * W < 16;
   using FS = FourStep<P, PAD>;
+  static constexpr int NI = FwdIn<FS, HALF>::NI;   // staged inputs per thread and field
   // shared memory: fixed-spectra tile [7][W][P], transform exchange [2W][CS],
-  // two stages of field inputs [2][N1/2][NT] and, where it does not cost a
+  // two stages of field inputs [2][NI][NT] and, where it does not cost a
   // second block per SM, the twiddle table [P] (else twiddles come from L1)
-  static constexpr size_t smem_base =
-      ((size_t)7 * W * P + (size_t)2 * W * FS::CS + (size_t)2 * (Split<P>::N1 / 2) * NT) * sizeof(float2);
+  static constexpr size_t smem_base = zmac_smem_base<P, HALF>(W);
   static constexpr bool fits2(size_t b) { return 2 * (b + 1024) <= 228 * 1024; }   // per-block reserve
   static constexpr bool TWS = fits2(smem_base + P * sizeof(float2)) || !fits2(smem_base);
   static constexpr size_t smem_bytes = smem_base + (TWS ? P * sizeof(float2) : 0);
@@ -276,14 +346,16 @@ struct ZmacCfg {
   static constexpr int MIN_BLOCKS = (fits2(smem_bytes) && regs_for(2) >= 128) ? 2 : 1;
 };
 
-template <int P, bool BF>
-__global__ void __launch_bounds__(ZmacCfg<P>::NT, ZmacCfg<P>::MIN_BLOCKS)
+template <int P, bool BF, bool HALF>
+__global__ void __launch_bounds__(ZmacCfg<P, HALF>::NT, ZmacCfg<P, HALF>::MIN_BLOCKS)
 k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot, const int* __restrict__ bounds) {
-  using FS = typename ZmacCfg<P>::FS;
-  constexpr int W = ZmacCfg<P>::W;
-  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FS::H;
-  constexpr int NC = 2 * W, NT = ZmacCfg<P>::NT, MI = (W * P + NT - 1) / NT;
+  using C = ZmacCfg<P, HALF>;
+  using FS = typename C::FS;
+  using FI = FwdIn<FS, HALF>;
+  constexpr int W = C::W;
+  constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = C::NI;
+  constexpr int NC = 2 * W, NT = C::NT, MI = (W * P + NT - 1) / NT;
   constexpr int TILE = W * P;                 // complex values per fixed-spectra tile
   extern __shared__ __align__(16) float2 smem[];
   float2* uvs = smem;                         // [7][W][P] fixed-spectra weights
@@ -313,7 +385,7 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   const bool has2 = t < NC * N1;
   const int c2 = t % NC, k1 = t / NC;
 
-  // z = N2*n1 + n2 < nz <= P/2 only for n1 < N1/2.  Field inputs are copied
+  // z = N2*n1 + n2 < nz (with nz <= P/2 only n1 < N1/2).  Field inputs are copied
   // asynchronously (cp.async) two fields ahead into this thread's own slots of
   // two stages: no registers are held meanwhile.  Slots outside the volume are
   // zero once and never copied to.  Fields run in the order (r, j), j < nfr(r).
@@ -376,7 +448,7 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   }
   fetch(stage);
   fetch(stage + H * NT);
-  constexpr bool TWS = ZmacCfg<P>::TWS;
+  constexpr bool TWS = C::TWS;
   if constexpr (TWS)
     for (int q = t; q < P; q += NT) tws[q] = __ldg(&tw[q]);
   const float2* twz = TWS ? tws : tw;
@@ -399,7 +471,7 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
       float2* buf = stage + (f & 1) * H * NT;
       float2 v[H];
       take(v, buf, j);
-      FS::template step1_half<-1, TWS>(v, ex + c1 * CS, n2, twz);
+      FI::template step1<-1, TWS>(v, ex + c1 * CS, n2, twz);
       __syncthreads();                         // (also orders this thread's reads of buf
                                                //  before the next copies into it)
       fetch(buf);                              // two fields ahead
@@ -476,8 +548,8 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
         const int lo = bounds ? bounds[6 * r] : 0, hi = bounds ? bounds[6 * r + 1] : g.vz - 1;
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
-          const int vz = shift_slot(k1 + N1 * k2, g.nz, P);
-          if (vz >= lo && vz <= hi) dst[(long long)vz * g.Py] = u[k2];
+          const int vz = shift_slot(k1 + N1 * k2, g.nz, P, lo, hi);
+          if (vz >= 0) dst[(long long)vz * g.Py] = u[k2];
         }
       }
     }
@@ -485,18 +557,25 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   }
 }
 
+template <int P, bool HALF>
+void launch_zmac_t(const void* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
+                   const int* bounds, cudaStream_t st) {
+  using C = ZmacCfg<P, HALF>;
+  dim3 grid((unsigned)((g.Py + C::W - 1) / C::W), (unsigned)(g.Px / 2 + 1));
+  if (g.bf16) {
+    set_smem(k_zmac<P, true, HALF>, C::smem_bytes);
+    k_zmac<P, true, HALF><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
+  } else {
+    set_smem(k_zmac<P, false, HALF>, C::smem_bytes);
+    k_zmac<P, false, HALF><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
+  }
+}
+
 template <int P>
 void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
                  const int* bounds, cudaStream_t st) {
-  using C = ZmacCfg<P>;
-  dim3 grid((unsigned)((g.Py + C::W - 1) / C::W), (unsigned)(g.Px / 2 + 1));
-  if (g.bf16) {
-    set_smem(k_zmac<P, true>, C::smem_bytes);
-    k_zmac<P, true><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
-  } else {
-    set_smem(k_zmac<P, false>, C::smem_bytes);
-    k_zmac<P, false><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
-  }
+  if (2 * g.nz <= P) launch_zmac_t<P, true>(F1, UV, F2, tw, g, nrot, bounds, st);
+  else launch_zmac_t<P, false>(F1, UV, F2, tw, g, nrot, bounds, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,11 +585,12 @@ void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw,
 // for the channel fields j < nch (channels a, b of the pair with their Eq. 6
 // weights, or Eq. 3 weights), and conj(A_mask) last, stored for kx <= Px/2.
 // ---------------------------------------------------------------------------
-template <int P, int W>
+template <int P, int W, bool HALF>
 __global__ void __launch_bounds__(2 * W * Split<P>::N2)
 k_prep_z(const float2* __restrict__ F1, float2* __restrict__ UV, const float2* __restrict__ tw,
          Geo g) {
   using FS = FourStep<P>;
+  using FI = FwdIn<FS, HALF>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
   constexpr int NC = 2 * W, NT = NC * N2, MI = (W * P + NT - 1) / NT;
   extern __shared__ float2 ex[];
@@ -534,14 +614,14 @@ k_prep_z(const float2* __restrict__ F1, float2* __restrict__ UV, const float2* _
     if (g.nch == 3) { wa = j == 2 ? 2.f : 1.f; wb = j == 0 ? 1.f : 2.f; }
     else { wb = j == 0 ? 1.f : 0.f; }
     const float2* src = F1 + (long long)j * g.nz * plane_stride;   // [j][kx][z][ky]
-    float2 v[FS::H];                      // z < nz <= P/2: upper half is zero
+    float2 v[FI::NI];                     // z < nz: with nz <= P/2 the upper half is zero
 #pragma unroll
-    for (int n1 = 0; n1 < FS::H; ++n1) {
+    for (int n1 = 0; n1 < FI::NI; ++n1) {
       const int z = N2 * n1 + n2;
       v[n1] = (ok1 && z < g.nz) ? src[((long long)kx1 * g.nz + z) * g.Py + ky1]
                                 : make_float2(0.f, 0.f);
     }
-    FS::template step1_half<-1>(v, ex + c1 * CS, n2, tw);
+    FI::template step1<-1>(v, ex + c1 * CS, n2, tw);
     __syncthreads();
     float2 u[N2];
     if (has2) FS::template step2<-1>(u, ex + c2 * CS, k1);
@@ -585,9 +665,13 @@ template <int P>
 void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g, cudaStream_t st) {
   constexpr int W = 8, N2 = Split<P>::N2;
   const size_t smem = (size_t)2 * W * FourStep<P>::CS * sizeof(float2);
-  set_smem(k_prep_z<P, W>, smem);
   dim3 grid((unsigned)((g.Py + W - 1) / W), (unsigned)(g.Px / 2 + 1));
-  k_prep_z<P, W><<<grid, 2 * W * N2, smem, st>>>(F1, UV, tw, g);
+  auto go = [&](auto kern) {
+    set_smem(kern, smem);
+    kern<<<grid, 2 * W * N2, smem, st>>>(F1, UV, tw, g);
+  };
+  if (2 * g.nz <= P) go(k_prep_z<P, W, true>);
+  else go(k_prep_z<P, W, false>);
 }
 
 // ---------------------------------------------------------------------------
@@ -631,8 +715,8 @@ k_inv_y(const float2* __restrict__ F2, float2* __restrict__ F3, const float2* __
       float2* dst = F3 + plane * (long long)g.vy * g.Px + kx;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
-        const int vy = shift_slot(k1 + N1 * k2, g.ny, P);
-        if (vy >= lo_y && vy <= hi_y) dst[(long long)vy * g.Px] = u[k2];
+        const int vy = shift_slot(k1 + N1 * k2, g.ny, P, lo_y, hi_y);
+        if (vy >= 0) dst[(long long)vy * g.Px] = u[k2];
       }
     }
   }
@@ -695,8 +779,8 @@ k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
       const unsigned row_lin = ((unsigned)vzi * (unsigned)g.vy + (unsigned)vyi) * (unsigned)g.vx;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
-        const int vxi = shift_slot(k1 + N1 * k2, g.nx, P);
-        if (vxi >= lo_x && vxi <= hi_x) {
+        const int vxi = shift_slot(k1 + N1 * k2, g.nx, P, lo_x, hi_x);
+        if (vxi >= 0) {
           const float2 zz = u[k2];
           float s = __int_as_float(0xff800000);
           if (zz.y >= th) {

@@ -51,6 +51,7 @@ struct Slot {                     // device resources of one volume shape
   int batch;
   int measure;
   int precision;
+  int pad_mode;
   cs_ngf_fixed* f = nullptr;
   float* dA = nullptr;
   uint8_t* dMA = nullptr;
@@ -126,7 +127,7 @@ bool same_shape(const Slot& s, const Job& j) {
   return std::memcmp(s.dims, j.dims, sizeof(s.dims)) == 0 &&
          std::memcmp(s.pad, j.pad, sizeof(s.pad)) == 0 && s.eps == j.cfg.eps &&
          s.gamma == j.cfg.gamma && s.batch == j.cfg.batch && s.measure == j.cfg.measure &&
-         s.precision == j.cfg.precision;
+         s.precision == j.cfg.precision && s.pad_mode == j.cfg.pad_mode;
 }
 
 void free_slot(Slot* s) {
@@ -191,7 +192,9 @@ cs_ngf_status setup_job(cs_ngf_server* sv, Job* j, Slot* slot, bool fresh) {
     return s;
   }
   if (cs_ngf_status s = csngf::detail::upload_rotations(slot->f, j->quats.data(), j->R, st)) return s;
-  return csngf::detail::pack_floating(slot->f, slot->dB, slot->dMB, st);
+  if (cs_ngf_status s = csngf::detail::pack_floating(slot->f, slot->dB, slot->dMB, st)) return s;
+  // FFT lengths for all of the job's rotations (bound-limited padding)
+  return csngf::detail::bound_pads(slot->f, j->R, st);
 }
 
 void finish_job(cs_ngf_server* sv, Job* j) {
@@ -245,6 +248,7 @@ Slot* find_slot(cs_ngf_server* sv, Job* j, bool* fresh) {
   s->batch = j->cfg.batch;
   s->measure = j->cfg.measure;
   s->precision = j->cfg.precision;
+  s->pad_mode = j->cfg.pad_mode;
   s->bytes = need;
   sv->bytes_in_use += need;
   sv->slots.push_back(std::move(s));

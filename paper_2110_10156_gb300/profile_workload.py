@@ -70,6 +70,7 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--traffic-from", help="summarise an ncu CSV log into profiles/ncu_traffic.json")
     ap.add_argument("--precision", choices=("fp32", "bf16"), default="fp32")
+    ap.add_argument("--pad-mode", choices=("bound", "full"), default="bound")
     ap.add_argument("--size", type=int, default=150)
     ap.add_argument("--rotations", type=int, default=2)
     ap.add_argument("--batch", type=int, default=2)
@@ -92,7 +93,8 @@ def main(argv=None) -> int:
                         max(3.0, 30 * n / 150), 30.0, max(1, int(20 * n / 150)),
                         args.rotations, masks="threshold")
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    f = cs_ngf.prepare_fixed(dev(p.A), dev(p.MA), batch=args.batch, precision=args.precision)
+    f = cs_ngf.prepare_fixed(dev(p.A), dev(p.MA), batch=args.batch, precision=args.precision,
+                             pad_mode=args.pad_mode)
     B, MB = dev(p.B), dev(p.MB)
     for _ in range(args.repeat):
         sc, sh = f.score_rotations(B, MB, p.quats)

@@ -41,13 +41,18 @@ def oracle150(pair150):
     return {r: O.score_map(p.A, p.MA, p.B, p.MB, p.quats[r], pad=(320, 320, 320))[0] for r in sample}
 
 
-@pytest.mark.parametrize("precision,tau", [("fp32", 1e-4), ("bf16", 1e-2)])
-def test_150_cubed_1000_rotations(cs, pair150, oracle150, precision, tau):
+@pytest.mark.parametrize("precision,tau,pad_mode", [("fp32", 1e-4, "bound"), ("bf16", 1e-2, "bound"),
+                                                    ("fp32", 1e-4, "full")])
+def test_150_cubed_1000_rotations(cs, pair150, oracle150, precision, tau, pad_mode):
     p = pair150
-    f = cs.prepare_fixed(dev(p.A), dev(p.MA), precision=precision)
-    assert f.pad == (320, 320, 320)
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), precision=precision, pad_mode=pad_mode)
+    assert f.max_pad == (320, 320, 320)
     assert f.sum_mask_a == int(p.MA.sum())
     sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+    if pad_mode == "full":
+        assert f.pad == (320, 320, 320)
+    else:                   # every shift the overlap bound admits lies within about +-60
+        assert all(v < 320 for v in f.pad), f.pad
     R = len(p.quats)
     assert sc.shape == (R,) and sh.shape == (R, 3)
     # properties at any size: scores are averages of values in [0, 1]; shifts in range

@@ -60,15 +60,21 @@ MAP_CASES = [
 ]
 
 
+def pad_mode_for(pad):
+    """Requested lengths are tested as given (full padding); automatic ones
+    with the default bound-limited padding."""
+    return "bound" if pad is None else "full"
+
+
 @pytest.mark.parametrize("dims,pad", MAP_CASES)
 def test_score_map_matches_oracle(cs, dims, pad):
     p = synth.small_pair(11 + sum(dims), dims, masks="threshold")
-    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad)
-    if pad is not None:
-        assert f.pad == tuple(pad)
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, pad_mode=pad_mode_for(pad))
     for q in (IDENTITY, p.q_true, rand_quat(sum(dims))):
         gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
-        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad)
+        if pad is not None:
+            assert f.pad == tuple(pad)
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad)
         check_maps(omap, gmap)
     f.release()
 
@@ -147,7 +153,8 @@ def test_quarter_turn_equals_identity_map(cs, axis):
     R = np.rint(O.quat_to_rotmat(q)).astype(int)
     B = _permute(p.A, R).astype(np.float32)
     MB = _permute(p.MA, R).astype(np.uint8)
-    f = cs.prepare_fixed(dev(p.A), dev(p.MA))
+    # one FFT geometry for both maps (bound-limited lengths follow each call's masks)
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad_mode="full")
     m_rot = f.score_map(dev(B), dev(MB), q).cpu().numpy()
     m_id = f.score_map(dev(p.A), dev(p.MA), IDENTITY).cpu().numpy()
     np.testing.assert_array_equal(m_rot, m_id)
@@ -229,14 +236,14 @@ def test_graph_replay_matches_direct_launches(cs):
 @pytest.mark.parametrize("dims,pad", [((12, 10, 14), None), ((20, 17, 23), None), ((9, 8, 10), (400, 32, 160))])
 def test_unsquared_measure_matches_oracle(cs, dims, pad):
     p = synth.small_pair(211 + sum(dims), dims, masks="threshold")
-    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, measure="unsquared")
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, measure="unsquared", pad_mode=pad_mode_for(pad))
     for q in (IDENTITY, p.q_true, rand_quat(7)):
         gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
-        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad, measure="unsquared")
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad, measure="unsquared")
         check_maps(omap, gmap)
     sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
     for r, q in enumerate(p.quats):
-        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad, measure="unsquared")
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad, measure="unsquared")
         check_best_against_map(omap, sc[r], sh[r])
 
 
@@ -257,14 +264,14 @@ TAU_BF16 = 1e-2
 @pytest.mark.parametrize("dims,pad", [((12, 10, 14), None), ((20, 17, 23), None), ((16, 15, 14), (320, 320, 320))])
 def test_bf16_form_within_reduced_precision_tolerance(cs, dims, pad):
     p = synth.small_pair(331 + sum(dims), dims, masks="threshold")
-    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, precision="bf16")
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, precision="bf16", pad_mode=pad_mode_for(pad))
     worst = 0.0
     for q in (IDENTITY, p.q_true, rand_quat(3)):
         gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
-        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad)
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad)
         worst = max(worst, check_maps(omap, gmap, tau=TAU_BF16))
     sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
     for r, q in enumerate(p.quats):
-        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=f.pad)
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad)
         check_best_against_map(omap, sc[r], sh[r], tau=TAU_BF16)
     assert worst > 0.0          # the reduced-precision path really differs from FP32 arithmetic

@@ -470,3 +470,36 @@ def test_slab_bound_never_below_overlap(seed):
     for idx in itertools.product(*[range(2 * n - 1) for n in dims]):
         chi = [i - (n - 1) for i, n in zip(idx, dims)]
         assert N[idx] <= min(bounds[ax][chi[ax]] for ax in range(3))
+
+
+# --------------------------------------- bound-limited FFT length (alias-free)
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_shorter_circular_length_is_exact_on_a_shift_range(seed):
+    """A length-P circular correlation holds at slot chi mod P the sum of the
+    linear one over chi + kP.  For shifts in [lo, hi] with P >= n + max(-lo,
+    hi), every chi + kP (k != 0) leaves the linear support [-(n-1), n-1], so
+    the slots equal the linear correlation there (checked against the direct
+    sum); one slot shorter, a boundary shift picks up an alias (positive
+    inputs make every linear value nonzero)."""
+    rng = np.random.default_rng(seed)
+    dims = tuple(int(v) for v in rng.integers(5, 9, size=3))
+    a = rng.random(dims) + 0.1
+    b = rng.random(dims) + 0.1
+    lo = [int(rng.integers(-(n - 1), 1)) for n in dims]
+    hi = [int(rng.integers(0, n)) for n in dims]
+    P = [n + max(-l, h) for n, l, h in zip(dims, lo, hi)]
+    box = tuple(slice(l + n - 1, h + n) for l, h, n in zip(lo, hi, dims))
+    ref = np.zeros(tuple(2 * n - 1 for n in dims))
+    for chi in itertools.product(*[range(-(n - 1), n) for n in dims]):
+        sa, sb = O._shift_slices(chi, dims, dims)
+        ref[tuple(c + n - 1 for c, n in zip(chi, dims))] = float((a[sa] * b[sb]).sum())
+    got = O.correlate_fft(a, b, tuple(P))
+    np.testing.assert_allclose(got[box], ref[box], rtol=1e-12, atol=1e-12)
+    for ax in range(3):
+        if P[ax] - 1 < dims[ax]:
+            continue
+        short = list(P)
+        short[ax] -= 1
+        bad = O.correlate_fft(a, b, tuple(short))
+        assert np.max(np.abs(bad[box] - ref[box])) > 1e-3
+
