@@ -86,14 +86,17 @@ typedef enum {
  * N(chi) <= sum_i min(a_i, b_{i + chi}) along each axis, a the slab counts of
  * M_A and b those of the rotated mask.  Each scoring call first counts the
  * rotated masks of all its rotations, takes the range [lo, hi] of shifts the
- * bound admits over all of them, and uses per axis the shortest supported
- * length P >= n + max(-lo, hi).  Then for every admitted shift chi the other
+ * bound admits for each of them, and gives each rotation per axis the
+ * shortest supported length P >= n + max(-lo, hi) over its own range.
+ * Rotations needing the same lengths are scored together (small groups join
+ * a larger one, with lengths raised to cover both), and the results come
+ * back in the caller's order.  Then for every admitted shift chi the other
  * shifts chi + kP, k != 0, fall outside [-(n-1), n-1] where the linear
  * correlation lives, so its slot holds exactly its own value; shifts outside
  * the range are invalid and reported as such, as with FULL.  Scores agree
  * with FULL up to FP32 rounding.  The call synchronises its stream once to
- * read the range, and recomputes the fixed spectra (about the cost of one
- * rotation) when the length changes. */
+ * read the ranges, and once more for each further set of lengths, whose
+ * fixed spectra it recomputes (about the cost of one rotation each). */
 typedef enum {
   CS_NGF_PAD_FULL = 0,  /* P >= 2n - 1 on every call */
   CS_NGF_PAD_BOUND = 1  /* per call, the shortest length the shift bound allows (default) */
@@ -124,6 +127,8 @@ typedef struct {
   int64_t workspace_bytes;      /* device bytes of the per-batch workspace */
   int32_t max_pad[3];           /* largest FFT lengths (buffers are sized for them) */
   int32_t pad_mode;             /* cs_ngf_pad_mode */
+  int32_t length_sets;          /* sets of FFT lengths the last scoring call used */
+  int32_t reserved_;
 } cs_ngf_info;
 
 /* Fill *cfg with the paper's settings (eps 1e-5, gamma 0.5, automatic pad and
@@ -310,12 +315,15 @@ cs_ngf_status cs_ngf_server_submit(cs_ngf_server* s, const float* A, const uint8
                                    const double* quats, int32_t R, const cs_ngf_config* cfg,
                                    int64_t* job_id);
 /* Ask a job to stop: a pending job never starts, a running job stops after
- * its launch groups in flight (its result then covers the scored prefix). */
+ * its launch groups in flight (its result then covers the rotations scored
+ * so far: a prefix of the job's rotations, or with bound-limited padding,
+ * which scores them grouped by FFT lengths, any subset, the others -inf). */
 cs_ngf_status cs_ngf_server_cancel(cs_ngf_server* s, int64_t job_id);
 /* Wait up to timeout_s seconds (negative = no limit) for a job; on return OK
  * the job's result is in *res (its own status in res->status) and, if not
- * NULL, its per-rotation results in host best_score [R] / best_shift [R][3];
- * the job is then forgotten.  ETIMEOUT if it did not finish in time. */
+ * NULL, its per-rotation results in host best_score [R] / best_shift [R][3]
+ * (-inf and (0, 0, 0) for rotations not scored); the job is then forgotten.
+ * ETIMEOUT if it did not finish in time. */
 cs_ngf_status cs_ngf_server_wait(cs_ngf_server* s, int64_t job_id, double timeout_s,
                                  cs_ngf_job_result* res, float* best_score, int32_t* best_shift);
 cs_ngf_status cs_ngf_server_stats(cs_ngf_server* s, cs_ngf_server_info* info);

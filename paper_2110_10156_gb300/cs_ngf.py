@@ -54,7 +54,8 @@ class Info(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("pad", ctypes.c_int32 * 3),
                 ("batch", ctypes.c_int32), ("sum_mask_a", ctypes.c_int64),
                 ("fixed_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("max_pad", ctypes.c_int32 * 3), ("pad_mode", ctypes.c_int32)]
+                ("max_pad", ctypes.c_int32 * 3), ("pad_mode", ctypes.c_int32),
+                ("length_sets", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -237,6 +238,12 @@ class Fixed:
         """FFT lengths (z, y, x) in use: those of the last call (bound-limited
         padding may shorten them below max_pad)."""
         return tuple(self._info().pad)
+
+    @property
+    def length_sets(self):
+        """Sets of FFT lengths the last scoring call used (rotations regrouped
+        by the lengths they need under bound-limited padding)."""
+        return int(self._info().length_sets)
 
     @property
     def handle(self):
@@ -451,8 +458,8 @@ class Server:
         out = dict(status=int(res.status), rotations=int(res.rotations), scored=int(res.scored),
                    score=float(res.score), rot_index=int(res.rot_index), shift=tuple(res.shift),
                    latency_ms=float(res.latency_ms), queue_ms=float(res.queue_ms))
-        if per_rotation:
-            out["scores"], out["shifts"] = sc[: res.scored], sh[: res.scored]
+        if per_rotation:                    # -inf / (0, 0, 0) where a rotation was not scored
+            out["scores"], out["shifts"] = sc, sh
         return out
 
     def stats(self):

@@ -180,6 +180,12 @@ void free_handle(cs_ngf_fixed* f) {
   if (f->rot_ev) cudaEventSynchronize(f->rot_ev);
   for (auto& sp : f->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
   if (f->gexec) cudaGraphExecDestroy(f->gexec);
+  for (auto& gs : f->graphs) cudaGraphExecDestroy(gs.exec);
+  cudaFree(f->allb);
+  cudaFreeHost(f->allb_h);
+  cudaFree(f->perm_d);
+  cudaFree(f->perm_score);
+  cudaFree(f->perm_shift);
   cudaFree(f->rot_slot);
   cudaFree(f->slot_score);
   cudaFree(f->slot_shift);
@@ -192,8 +198,6 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->res_shift);
   cudaFree(f->A_keep);
   cudaFree(f->MA_keep);
-  cudaFree(f->ubound);
-  cudaFreeHost(f->ubound_h);
   delete f;
 }
 
@@ -362,9 +366,11 @@ cs_ngf_status run_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* MA, cuda
   int sumA = 0;
   CS_CUDA(cudaMemcpyAsync(&sumA, f->msum, sizeof(int), cudaMemcpyDeviceToHost, st));
   CS_CUDA(cudaStreamSynchronize(st));
-  if (f->gexec && sumA != f->sumA) {     // the captured threshold launch holds sum(M_A)
-    cudaGraphExecDestroy(f->gexec);
+  if (sumA != f->sumA) {                 // the captured threshold launch holds sum(M_A)
+    if (f->gexec) cudaGraphExecDestroy(f->gexec);
     f->gexec = nullptr;
+    for (auto& gs : f->graphs) cudaGraphExecDestroy(gs.exec);
+    f->graphs.clear();
   }
   f->sumA = sumA;
   return CS_NGF_OK;
@@ -380,58 +386,89 @@ cs_ngf_status set_pads(cs_ngf_fixed* f, const int pad[3], cudaStream_t st) {
   for (int a = 0; a < 3; ++a)
     if (cur[a] != pad[a])
       if (cs_ngf_status s = fill_twiddles(pad[a], f->tw[a])) return s;
+  // the captured launches hold the lengths: keep this graph for a later
+  // return to them, and take the one of the new lengths if there is one
+  if (f->gexec) f->graphs.push_back({{g.Pz, g.Py, g.Px}, f->gexec});
+  f->gexec = nullptr;
+  for (size_t i = 0; i < f->graphs.size(); ++i)
+    if (std::equal(pad, pad + 3, f->graphs[i].pad)) {
+      f->gexec = f->graphs[i].exec;
+      f->graphs.erase(f->graphs.begin() + (long)i);
+      break;
+    }
   g.Pz = pad[0];
   g.Py = pad[1];
   g.Px = pad[2];
-  if (f->gexec) {                                // the captured launches hold the old lengths
-    cudaGraphExecDestroy(f->gexec);
-    f->gexec = nullptr;
-  }
   return run_fixed(f, f->A_keep, f->MA_keep, st);
 }
 
-// Section 3.2 minimum overlap -> FFT lengths: the union over the R uploaded
-// rotations of the slab-bound shift ranges (the same counts and bound the
-// launch groups compute), then per axis the shortest supported length
-// P >= n + max(-chi_lo, chi_hi), at most alloc_pad
-cs_ngf_status bound_pads_impl(cs_ngf_fixed* f, int R, cudaStream_t st) {
-  if (f->pad_mode != CS_NGF_PAD_BOUND) return CS_NGF_OK;
+// the shortest supported length >= need, at most cap
+int length_for(int need, int cap) {
+  for (int v : kPads)
+    if (v >= need) return std::min(v, cap);
+  return cap;
+}
+
+cs_ngf_status ensure_rotation_buffers(cs_ngf_fixed* f, int R) {
+  if (R <= f->allb_cap) return CS_NGF_OK;
+  CS_CUDA(cudaDeviceSynchronize());              // the old buffers may still be read
+  cudaFree(f->allb);
+  cudaFreeHost(f->allb_h);
+  cudaFree(f->perm_d);
+  cudaFree(f->perm_score);
+  cudaFree(f->perm_shift);
+  f->allb = f->perm_d = f->allb_h = nullptr;
+  f->perm_score = nullptr;
+  f->perm_shift = nullptr;
+  f->allb_cap = 0;
+  const int cap = std::max(R, 64);
+  CS_CUDA(dalloc(&f->allb, (size_t)cap * 6));
+  CS_CUDA(cudaMallocHost((void**)&f->allb_h, sizeof(int) * 6 * (size_t)cap));
+  CS_CUDA(dalloc(&f->perm_d, (size_t)cap));
+  CS_CUDA(dalloc(&f->perm_score, (size_t)cap));
+  CS_CUDA(dalloc(&f->perm_shift, (size_t)cap * 3));
+  f->allb_cap = cap;
+  return CS_NGF_OK;
+}
+
+// Section 3.2 shift bounds of each of the R uploaded rotations (the same
+// counts and bound the launch groups compute) into f->allb_h [R][6];
+// synchronises st
+cs_ngf_status rotation_bounds(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st) {
+  if (cs_ngf_status s = ensure_rotation_buffers(f, R)) return s;
   const Geo& g = f->g;
   const size_t nmarg = (size_t)g.nz + g.ny + g.nx;
-  { Stage sp(f, 7, st); k_bound_reset<<<1, 32, 0, st>>>(f->ubound); }
-  if (cs_ngf_status s = check_launch("bound reset")) return s;
   for (int r0 = 0; r0 < R; r0 += f->batch) {
     const int nb = std::min(f->batch, R - r0);
     CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int) * nb, st));
     CS_CUDA(cudaMemsetAsync(f->margB, 0, sizeof(int) * nmarg * nb, st));
     {
       Stage sp(f, 0, st);
-      k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, f->rot_d + r0, g, nullptr, nullptr,
-                                                       f->msum, f->margB);
+      k_mask_counts<<<resample_grid(g, nb), 128, 0, st>>>(MB, f->rot_d + r0, g, f->msum, f->margB);
     }
     if (cs_ngf_status s = check_launch("mask counts")) return s;
     {
       Stage sp(f, 7, st);
       k_shift_bounds<<<dim3((unsigned)nb, 3u), 512, 0, st>>>(f->margA, f->margB, f->msum, f->sumA,
-                                                             f->gamma, g, f->bounds);
+                                                             f->gamma, g, f->allb + 6 * (size_t)r0);
     }
     if (cs_ngf_status s = check_launch("shift bounds")) return s;
-    { Stage sp(f, 7, st); k_bound_union<<<(nb + 127) / 128, 128, 0, st>>>(f->bounds, nb, f->ubound); }
-    if (cs_ngf_status s = check_launch("bound union")) return s;
   }
-  CS_CUDA(cudaMemcpyAsync(f->ubound_h, f->ubound, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaMemcpyAsync(f->allb_h, f->allb, sizeof(int) * 6 * (size_t)R, cudaMemcpyDeviceToHost, st));
   CS_CUDA(cudaStreamSynchronize(st));
-  const int dims[3] = {g.nz, g.ny, g.nx};
-  int pad[3];
+  return CS_NGF_OK;
+}
+
+// FFT lengths one rotation needs: per axis the shortest supported P >=
+// n + max(-chi_lo, chi_hi) over its admitted shifts; false if it admits none
+bool rotation_lengths(const cs_ngf_fixed* f, const int* b, int pad[3]) {
+  const int dims[3] = {f->g.nz, f->g.ny, f->g.nx};
+  if (b[0] > b[1] || b[2] > b[3] || b[4] > b[5]) return false;
   for (int a = 0; a < 3; ++a) {
-    const int n = dims[a], lo = f->ubound_h[2 * a], hi = f->ubound_h[2 * a + 1];
-    // no rotation admits a shift: any length >= n gives the same (empty) result
-    const int need = lo > hi ? n : n + std::max(n - 1 - lo, hi - (n - 1));
-    pad[a] = f->alloc_pad[a];
-    for (int v : kPads)
-      if (v >= need) { pad[a] = std::min(v, f->alloc_pad[a]); break; }
+    const int n = dims[a], lo = b[2 * a], hi = b[2 * a + 1];
+    pad[a] = length_for(n + std::max(n - 1 - lo, hi - (n - 1)), f->alloc_pad[a]);
   }
-  return set_pads(f, pad, st);
+  return true;
 }
 
 cs_ngf_status check_volume_args(const cs_ngf_fixed* f, const float* B, const uint8_t* MB) {
@@ -462,14 +499,134 @@ cs_ngf_status score_range_impl(cs_ngf_fixed* f, int r0_begin, int n, float* best
   return CS_NGF_OK;
 }
 
+// Bound-limited padding per rotation: each rotation's own shortest lengths;
+// rotations that need the same lengths form one class, scored together.  A
+// class costs a fixed-spectra recomputation, a stream synchronisation and
+// (once per handle) a graph capture, about kClassCost rotations of its own
+// size; so two classes merge, with lengths raised to cover both, while the
+// cheapest merge adds less transform volume than that (and while there are
+// more than kMaxClasses).  Rotations admitting no shift join the first
+// class.  The classes do not depend on the launch-group size, so results
+// stay the same for every even batch.
+constexpr double kClassCost = 4.0;
+constexpr size_t kMaxClasses = 8;
+struct LengthClass { int pad[3]; std::vector<int> rot; };
+
+double class_volume(const int* p) { return (double)p[0] * p[1] * p[2]; }
+
+std::vector<LengthClass> length_classes(const cs_ngf_fixed* f, int R) {
+  std::vector<LengthClass> cls;
+  std::vector<int> none;
+  for (int r = 0; r < R; ++r) {
+    int p[3];
+    if (!rotation_lengths(f, f->allb_h + 6 * (size_t)r, p)) { none.push_back(r); continue; }
+    size_t k = 0;
+    while (k < cls.size() && !std::equal(p, p + 3, cls[k].pad)) ++k;
+    if (k == cls.size()) cls.push_back({{p[0], p[1], p[2]}, {}});
+    cls[k].rot.push_back(r);
+  }
+  while (cls.size() > 1) {
+    size_t bc = 0, bd = 1;
+    double best = -1.0;
+    int bm[3] = {0, 0, 0};
+    for (size_t c = 0; c < cls.size(); ++c)
+      for (size_t d = c + 1; d < cls.size(); ++d) {
+        int m[3];
+        for (int a = 0; a < 3; ++a) m[a] = std::max(cls[c].pad[a], cls[d].pad[a]);
+        const double cost = (class_volume(m) - class_volume(cls[c].pad)) * cls[c].rot.size() +
+                            (class_volume(m) - class_volume(cls[d].pad)) * cls[d].rot.size();
+        if (best < 0.0 || cost < best) {
+          best = cost;
+          bc = c;
+          bd = d;
+          std::copy(m, m + 3, bm);
+        }
+      }
+    const double keep = kClassCost * std::min(class_volume(cls[bc].pad), class_volume(cls[bd].pad));
+    if (best >= keep && cls.size() <= kMaxClasses) break;
+    std::copy(bm, bm + 3, cls[bc].pad);
+    cls[bc].rot.insert(cls[bc].rot.end(), cls[bd].rot.begin(), cls[bd].rot.end());
+    std::sort(cls[bc].rot.begin(), cls[bc].rot.end());
+    cls.erase(cls.begin() + (long)bd);
+  }
+  if (cls.empty()) {
+    LengthClass lc;
+    for (int a = 0; a < 3; ++a) lc.pad[a] = length_for(a == 0 ? f->g.nz : a == 1 ? f->g.ny : f->g.nx,
+                                                       f->alloc_pad[a]);
+    cls.push_back(lc);
+  }
+  cls[0].rot.insert(cls[0].rot.end(), none.begin(), none.end());
+  std::sort(cls[0].rot.begin(), cls[0].rot.end());
+  // start with the lengths in use (no recomputation), then the larger classes
+  std::stable_sort(cls.begin(), cls.end(), [&](const LengthClass& a, const LengthClass& b) {
+    const int cur[3] = {f->g.Pz, f->g.Py, f->g.Px};
+    const bool ca = std::equal(a.pad, a.pad + 3, cur), cb = std::equal(b.pad, b.pad + 3, cur);
+    if (ca != cb) return ca;
+    return a.rot.size() > b.rot.size();
+  });
+  return cls;
+}
+
+// Length classes of the R uploaded rotations (floating mask MB, device):
+// bounds (synchronises st), classes, and the rotation matrices re-uploaded
+// in class order when there is more than one.  perm[i] = original index of
+// the i-th rotation in class order (empty if the order is unchanged); class
+// c covers [ends[c-1], ends[c]) with lengths pads[c].  Without bound-limited
+// padding: one class with the lengths in use.
+cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st,
+                           std::vector<int>& perm, std::vector<int>& ends, std::vector<int>& pads) {
+  perm.clear();
+  ends.assign(1, R);
+  pads.assign({f->g.Pz, f->g.Py, f->g.Px});
+  f->length_sets = 1;
+  if (f->pad_mode != CS_NGF_PAD_BOUND) return CS_NGF_OK;
+  if (cs_ngf_status s = rotation_bounds(f, MB, R, st)) return s;
+  std::vector<LengthClass> cls = length_classes(f, R);
+  f->length_sets = (int)cls.size();
+  ends.clear();
+  pads.clear();
+  int k = 0;
+  for (const auto& c : cls) {
+    k += (int)c.rot.size();
+    ends.push_back(k);
+    pads.insert(pads.end(), c.pad, c.pad + 3);
+  }
+  if (cls.size() == 1) return CS_NGF_OK;
+  // the stream is idle (rotation_bounds waited for it): rot_h is free
+  std::vector<RotMat> orig(f->rot_h, f->rot_h + R);
+  perm.reserve(R);
+  k = 0;
+  for (const auto& c : cls)
+    for (int r : c.rot) { f->rot_h[k++] = orig[r]; perm.push_back(r); }
+  CS_CUDA(cudaMemcpyAsync(f->rot_d, f->rot_h, sizeof(RotMat) * R, cudaMemcpyHostToDevice, st));
+  CS_CUDA(cudaEventRecord(f->rot_ev, st));
+  return CS_NGF_OK;
+}
+
 cs_ngf_status score_all(cs_ngf_fixed* f, const float* B, const uint8_t* MB, const double* quats,
                         int R, float* best_score, int32_t* best_shift, cudaStream_t st) {
   if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
   if (!best_score || !best_shift) return fail(CS_NGF_EINVAL, "output pointer is NULL");
   if (cs_ngf_status s = upload_rotations(f, quats, R, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, MB, st)) return s;
-  if (cs_ngf_status s = bound_pads_impl(f, R, st)) return s;
-  return score_range_impl(f, 0, R, best_score, best_shift, st);
+  std::vector<int> perm, ends, pads;
+  if (cs_ngf_status s = plan_classes(f, MB, R, st, perm, ends, pads)) return s;
+  if (perm.empty()) {
+    if (cs_ngf_status s = set_pads(f, pads.data(), st)) return s;
+    return score_range_impl(f, 0, R, best_score, best_shift, st);
+  }
+  // classes one after another into the handle's buffers, then scattered to
+  // the caller's order
+  std::copy(perm.begin(), perm.end(), f->allb_h);   // pinned staging; the bounds are spent
+  CS_CUDA(cudaMemcpyAsync(f->perm_d, f->allb_h, sizeof(int) * R, cudaMemcpyHostToDevice, st));
+  int r0 = 0;
+  for (size_t c = 0; c < ends.size(); ++c) {
+    if (cs_ngf_status s = set_pads(f, pads.data() + 3 * c, st)) return s;
+    if (cs_ngf_status s = score_range_impl(f, r0, ends[c] - r0, f->perm_score, f->perm_shift, st)) return s;
+    r0 = ends[c];
+  }
+  { Stage sp(f, 7, st); k_scatter_results<<<(R + 255) / 256, 256, 0, st>>>(f->perm_d, f->perm_score, f->perm_shift, R, best_score, best_shift); }
+  return check_launch("scatter results");
 }
 
 cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
@@ -549,8 +706,12 @@ cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int
                           cudaStream_t st) {
   return ::score_range_impl(f, r0, n, best_score, best_shift, st);
 }
-cs_ngf_status bound_pads(cs_ngf_fixed* f, int R, cudaStream_t st) {
-  return ::bound_pads_impl(f, R, st);
+cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st,
+                           std::vector<int>& perm, std::vector<int>& ends, std::vector<int>& pads) {
+  return ::plan_classes(f, MB, R, st, perm, ends, pads);
+}
+cs_ngf_status set_lengths(cs_ngf_fixed* f, const int pad[3], cudaStream_t st) {
+  return ::set_pads(f, pad, st);
 }
 cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
   return ::resolve_pads_impl(dims, cfg, pad);
@@ -670,8 +831,6 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   if (f->pad_mode == CS_NGF_PAD_BOUND) {
     CS_TRYC(dalloc(&f->A_keep, (size_t)g.nvox));
     CS_TRYC(dalloc(&f->MA_keep, (size_t)g.nvox));
-    CS_TRYC(dalloc(&f->ubound, (size_t)6));
-    CS_TRYC(cudaMallocHost((void**)&f->ubound_h, 6 * sizeof(int)));
     CS_TRYC(cudaMemcpyAsync(f->A_keep, A, sizeof(float) * g.nvox, cudaMemcpyDeviceToDevice, st));
     CS_TRYC(cudaMemcpyAsync(f->MA_keep, maskA, (size_t)g.nvox, cudaMemcpyDeviceToDevice, st));
     f->fixed_bytes += (size_t)g.nvox * 5;
@@ -759,7 +918,9 @@ cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* m
   if (cs_ngf_status s = ensure_results(f, 1)) return s;
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
-  if (cs_ngf_status s = bound_pads_impl(f, 1, st)) return s;
+  std::vector<int> perm, ends, pads;
+  if (cs_ngf_status s = plan_classes(f, maskB, 1, st, perm, ends, pads)) return s;
+  if (cs_ngf_status s = set_pads(f, pads.data(), st)) return s;
   return score_batch(f, 0, 1, f->res_score, f->res_shift, map, st);
 }
 
@@ -788,6 +949,8 @@ cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info) {
   info->workspace_bytes = (int64_t)f->workspace_bytes;
   for (int a = 0; a < 3; ++a) info->max_pad[a] = f->alloc_pad[a];
   info->pad_mode = f->pad_mode;
+  info->length_sets = f->length_sets;
+  info->reserved_ = 0;
   return CS_NGF_OK;
 }
 

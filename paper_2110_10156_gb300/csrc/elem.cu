@@ -44,9 +44,9 @@ __global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict
     BM[i] = make_float2(B[i], MB[i] ? 1.0f : 0.0f);
 }
 
-__device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, const RotMat& R,
-                                               const Geo& g, int x, int y, int z, float& val,
-                                               uint8_t& m) {
+// sample point p = R (x - c) + c of voxel (x, y, z) per axis (FP32, fixed order)
+__device__ __forceinline__ void sample_axes(const RotMat& R, const Geo& g, int x, int y, int z,
+                                            AxisSample& ax, AxisSample& ay, AxisSample& az) {
   const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1),
               cz = 0.5f * (float)(g.nz - 1);
   const float dx = __fsub_rn((float)x, cx), dy = __fsub_rn((float)y, cy),
@@ -59,7 +59,35 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
     acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 2], dz));
     p[i] = __fadd_rn(acc, i == 0 ? cx : (i == 1 ? cy : cz));
   }
-  AxisSample ax = axis_sample(p[0], g.nx), ay = axis_sample(p[1], g.ny), az = axis_sample(p[2], g.nz);
+  ax = axis_sample(p[0], g.nx);
+  ay = axis_sample(p[1], g.ny);
+  az = axis_sample(p[2], g.nz);
+}
+
+// the rotated mask alone, from the 0/1 bytes of M_B: the same sample point
+// and the same lerp sequence as resample_voxel, so the same decision
+__device__ __forceinline__ uint8_t mask_voxel(const uint8_t* __restrict__ MB, const RotMat& R,
+                                              const Geo& g, int x, int y, int z) {
+  AxisSample ax, ay, az;
+  sample_axes(R, g, x, y, z, ax, ay, az);
+  if (!(ax.inside && ay.inside && az.inside)) return 0;
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  const long long b000 = (long long)az.i0 * sz + (long long)ay.i0 * sy + ax.i0;
+  const long long o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+  float c[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c[k] = __ldg(&MB[b000 + o[k]]) ? 1.0f : 0.0f;
+  float m00 = lerp_rn(c[0], c[1], ax.t), m01 = lerp_rn(c[2], c[3], ax.t);
+  float m10 = lerp_rn(c[4], c[5], ax.t), m11 = lerp_rn(c[6], c[7], ax.t);
+  float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
+  return lerp_rn(m0, m1, az.t) >= 0.5f ? 1 : 0;
+}
+
+__device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, const RotMat& R,
+                                               const Geo& g, int x, int y, int z, float& val,
+                                               uint8_t& m) {
+  AxisSample ax, ay, az;
+  sample_axes(R, g, x, y, z, ax, ay, az);
   val = 0.0f;
   m = 0;
   if (ax.inside && ay.inside && az.inside) {
@@ -90,10 +118,13 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
 // (block: 8 x 4 x 4*RZ voxels).  Mask counts per axis (the slab bound's
 // marginals) are reduced with warp shuffles before one atomic per slot.
 // Grid: (x tiles, y tiles, z tiles * rotations).
-__global__ void __launch_bounds__(128)
-k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
-           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
-           int* __restrict__ marg) {
+// MONLY: only the rotated mask, from M_B bytes, counted (no volumes written)
+template <bool MONLY>
+__device__ __forceinline__ void resample_block(const float2* __restrict__ BM,
+                                               const uint8_t* __restrict__ MB,
+                                               const RotMat* __restrict__ rot, const Geo& g,
+                                               float* __restrict__ Bh, uint8_t* __restrict__ Mh,
+                                               int* __restrict__ msum, int* __restrict__ marg) {
   constexpr int RZ = kResampleZGroups, ZB = 4 * RZ;    // z-planes per block
   const int ztiles = (g.nz + ZB - 1) / ZB;
   const int r = blockIdx.z / ztiles, zt = blockIdx.z - r * ztiles;
@@ -109,15 +140,17 @@ k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
     const int z = zt * ZB + 4 * k + wid;
     int mk = 0;
     if (x < g.nx && y < g.ny && z < g.nz) {
-      float val;
-      uint8_t m;
-      resample_voxel(BM, R, g, x, y, z, val, m);
-      if (Bh) {                                // NULL: mask counts only (bounds pre-pass)
+      if constexpr (MONLY) {
+        mk = mask_voxel(MB, R, g, x, y, z);
+      } else {
+        float val;
+        uint8_t m;
+        resample_voxel(BM, R, g, x, y, z, val, m);
         const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
         Bh[idx] = val;
         Mh[idx] = m;
+        mk = m;
       }
-      mk = m;
     }
     c += mk;
     const int wz = __reduce_add_sync(0xffffffffu, mk);      // plane z, this warp's patch
@@ -155,6 +188,19 @@ k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
       if (v) atomicAdd(&mr[g.nz + g.ny + blockIdx.x * 8 + q], v);
     }
   }
+}
+
+__global__ void __launch_bounds__(128)
+k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
+           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
+           int* __restrict__ marg) {
+  resample_block<false>(BM, nullptr, rot, g, Bh, Mh, msum, marg);
+}
+
+__global__ void __launch_bounds__(128)
+k_mask_counts(const uint8_t* __restrict__ MB, const RotMat* __restrict__ rot, Geo g,
+              int* __restrict__ msum, int* __restrict__ marg) {
+  resample_block<true>(nullptr, MB, rot, g, nullptr, nullptr, msum, marg);
 }
 
 __global__ void k_marginals(const uint8_t* __restrict__ M, Geo g, int* __restrict__ marg) {
@@ -202,20 +248,15 @@ __global__ void k_shift_bounds(const int* __restrict__ margA, const int* __restr
   }
 }
 
-__global__ void k_bound_reset(int* __restrict__ u) {
-  if (threadIdx.x < 6) u[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
-}
-
-__global__ void k_bound_union(const int* __restrict__ bounds, int nrot, int* __restrict__ u) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrot; r += gridDim.x * blockDim.x) {
-    const int* b = bounds + 6 * r;
-    if (b[0] > b[1] || b[2] > b[3] || b[4] > b[5]) continue;   // no shift can be valid
+__global__ void k_scatter_results(const int* __restrict__ perm, const float* __restrict__ score,
+                                  const int32_t* __restrict__ shift, int n,
+                                  float* __restrict__ out_score, int32_t* __restrict__ out_shift) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int r = perm[i];
+  out_score[r] = score[i];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      atomicMin(&u[2 * a], b[2 * a]);
-      atomicMax(&u[2 * a + 1], b[2 * a + 1]);
-    }
-  }
+  for (int a = 0; a < 3; ++a) out_shift[3 * (long long)r + a] = shift[3 * (long long)i + a];
 }
 
 __global__ void k_fill(float* __restrict__ p, long long n, float v) {

@@ -25,8 +25,18 @@ struct cs_ngf_fixed {
   int pad_mode = 0;
   float* A_keep = nullptr;     // copies of A and M_A: the fixed spectra are
   uint8_t* MA_keep = nullptr;  // recomputed when the lengths in use change
-  int* ubound = nullptr;       // device: union of a call's shift bounds [6]
-  int* ubound_h = nullptr;     // pinned host copy of it
+  // per-rotation shift bounds of a call and its rotations regrouped by FFT
+  // lengths (bound-limited padding), grown on demand to the call's R
+  int* allb = nullptr;         // device [R][6]
+  int* allb_h = nullptr;       // pinned host copy
+  int* perm_d = nullptr;       // device: original index of each regrouped rotation
+  float* perm_score = nullptr; // device results in regrouped order
+  int32_t* perm_shift = nullptr;
+  int allb_cap = 0;
+  int length_sets = 1;         // sets of FFT lengths the last scoring call used
+  // one captured graph per set of FFT lengths (all reference the same buffers)
+  struct GraphSlot { int pad[3]; cudaGraphExec_t exec; };
+  std::vector<GraphSlot> graphs;
   size_t f02_elems = 0, f13_elems = 0;
   float2* UV = nullptr;
   float* Bh = nullptr;
@@ -75,12 +85,18 @@ cs_ngf_status fail(cs_ngf_status s, const std::string& msg);
 cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* quats, int R, cudaStream_t st);
 // (B, M_B) -> f->BM for the following score calls
 cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st);
-// bound-limited padding: for the R uploaded rotations (B already packed),
-// bound the shifts that can be valid, pick per axis the shortest supported
-// FFT length that keeps all of them alias-free (at most alloc_pad) and switch
-// the handle to it (fixed spectra recomputed when it changes).  Synchronises
-// `st` once.  A no-op unless pad_mode is CS_NGF_PAD_BOUND.
-cs_ngf_status bound_pads(cs_ngf_fixed* f, int R, cudaStream_t st);
+// Bound-limited padding (pad_mode CS_NGF_PAD_BOUND): the R uploaded
+// rotations of the floating mask MB (device) grouped into classes by the FFT
+// lengths their admitted shifts need.  Synchronises `st`.  perm[i] is the
+// original index of the i-th rotation in class order (empty: order
+// unchanged; otherwise the device matrices are re-uploaded in that order);
+// class c covers [ends[c-1], ends[c]) and uses lengths pads[3c..3c+2].  In
+// other modes: one class with the lengths in use.
+cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st,
+                           std::vector<int>& perm, std::vector<int>& ends, std::vector<int>& pads);
+// switch the handle to FFT lengths pad (recomputing the fixed spectra if they
+// change; synchronises `st` then)
+cs_ngf_status set_lengths(cs_ngf_fixed* f, const int pad[3], cudaStream_t st);
 // score rotations [r0, r0 + n) of the uploaded set into best_score / best_shift
 // (device, indexed from r0), in launch groups of f->batch
 cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int32_t* best_shift,

@@ -90,11 +90,14 @@ __device__ __forceinline__ unsigned long long make_key(float s, unsigned lin) {
 // read as (value, mask) pairs prepared by k_pack_bm.
 __global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict__ MB, long long n,
                           float2* __restrict__ BM);
-// With Bh == NULL it writes no volumes and only counts the rotated masks
-// (msum, marg): the pre-pass that bounds the shifts of a whole call.
 __global__ void k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
                            float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
                            int* __restrict__ marg);
+// The rotated masks alone, counted into msum and marg as k_resample counts
+// them (same decisions, read from the 0/1 bytes of M_B, no volumes written):
+// the pre-pass that bounds the shifts of a whole call.  Grid: resample_grid.
+__global__ void k_mask_counts(const uint8_t* __restrict__ MB, const RotMat* __restrict__ rot, Geo g,
+                              int* __restrict__ msum, int* __restrict__ marg);
 constexpr int kResampleZGroups = 4;            // z-plane groups of 4 per resample block
 inline dim3 resample_grid(const Geo& g, int nrot) {
   return dim3((unsigned)((g.nx + 7) / 8), (unsigned)((g.ny + 3) / 4),
@@ -113,11 +116,11 @@ __global__ void k_shift_bounds(const int* __restrict__ margA, const int* __restr
                                const int* __restrict__ msumB, int sumA, float gamma, Geo g,
                                int* __restrict__ bounds);
 __global__ void k_fill(float* __restrict__ p, long long n, float v);
-// Union of the shift bounds of nrot rotations into u[6] = {lo_z, hi_z, lo_y,
-// hi_y, lo_x, hi_x} (slots v = chi + n - 1), over the rotations for which some
-// shift can be valid; k_bound_reset sets u to the empty range first.
-__global__ void k_bound_reset(int* __restrict__ u);
-__global__ void k_bound_union(const int* __restrict__ bounds, int nrot, int* __restrict__ u);
+// results scored in a regrouped order back to the caller's: entry i belongs
+// to rotation perm[i]
+__global__ void k_scatter_results(const int* __restrict__ perm, const float* __restrict__ score,
+                                  const int32_t* __restrict__ shift, int n,
+                                  float* __restrict__ out_score, int32_t* __restrict__ out_shift);
 
 // sum of a uint8 mask (for the fixed volume)
 __global__ void k_mask_sum(const uint8_t* __restrict__ M, long long n, int* __restrict__ out);

@@ -217,7 +217,9 @@ constexpr int pass_blocks(int threads, size_t smem, int minr) {
   return best;
 }
 template <int P> struct FwdYCfg {
-  static constexpr int W = 16;
+  // 16 columns per block; 8 where the second stage is longer than 20 points
+  // (more registers per thread: smaller blocks keep several per SM)
+  static constexpr int W = Split<P>::N2 > 20 ? 8 : 16;
   static constexpr int NT = W * Split<P>::N2;
   static constexpr size_t smem_bytes = (size_t)W * FourStep<P>::CS * sizeof(float2);
   // the 25- and 32-point second stages need more registers than 16- or 20-point ones

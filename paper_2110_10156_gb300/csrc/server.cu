@@ -86,6 +86,10 @@ struct Job {
   Slot* slot = nullptr;
   cudaStream_t stream = nullptr;
   int cursor = 0;
+  // bound-limited padding: rotations in class order (perm[i] = original
+  // index; empty = unchanged), class c ends at class_end[c], lengths class_pad
+  std::vector<int> perm, class_end, class_pad;
+  size_t cls = 0;
   std::deque<cudaEvent_t> inflight;
   cudaEvent_t done_ev = nullptr;
   bool results_enqueued = false;
@@ -193,8 +197,12 @@ cs_ngf_status setup_job(cs_ngf_server* sv, Job* j, Slot* slot, bool fresh) {
   }
   if (cs_ngf_status s = csngf::detail::upload_rotations(slot->f, j->quats.data(), j->R, st)) return s;
   if (cs_ngf_status s = csngf::detail::pack_floating(slot->f, slot->dB, slot->dMB, st)) return s;
-  // FFT lengths for all of the job's rotations (bound-limited padding)
-  return csngf::detail::bound_pads(slot->f, j->R, st);
+  // FFT lengths per class of rotations (bound-limited padding), first class set up
+  if (cs_ngf_status s = csngf::detail::plan_classes(slot->f, slot->dMB, j->R, st, j->perm, j->class_end,
+                                                    j->class_pad))
+    return s;
+  j->cls = 0;
+  return csngf::detail::set_lengths(slot->f, j->class_pad.data(), st);
 }
 
 void finish_job(cs_ngf_server* sv, Job* j) {
@@ -325,9 +333,18 @@ void worker_loop(cs_ngf_server* sv) {
       const bool stop_job = j->cancel || j->cursor >= j->R;
       if (!stop_job && (int)j->inflight.size() < sv->cfg.max_inflight) {
         Slot* s = j->slot;
-        const int n = std::min(s->f->batch, j->R - j->cursor);
+        // launch groups stay inside a class; the next class switches lengths
+        // (which waits for this job's groups in flight)
+        bool next_class = false;
+        while (j->cls + 1 < j->class_end.size() && j->cursor >= j->class_end[j->cls]) {
+          ++j->cls;
+          next_class = true;
+        }
+        const int n = std::min(s->f->batch, j->class_end[j->cls] - j->cursor);
         lk.unlock();
-        cs_ngf_status st = csngf::detail::score_range(s->f, j->cursor, n, s->d_score, s->d_shift, j->stream);
+        cs_ngf_status st = CS_NGF_OK;
+        if (next_class) st = csngf::detail::set_lengths(s->f, j->class_pad.data() + 3 * j->cls, j->stream);
+        if (!st) st = csngf::detail::score_range(s->f, j->cursor, n, s->d_score, s->d_shift, j->stream);
         cudaEvent_t ev = nullptr;
         if (!st) st = cuda_status(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
         if (!st) st = cuda_status(cudaEventRecord(ev, j->stream), "event record");
@@ -375,9 +392,19 @@ void worker_loop(cs_ngf_server* sv) {
         }
         const int n = j->cursor;
         Slot* s = j->slot;
-        j->out_score.assign(s->h_score, s->h_score + n);
-        j->out_shift.assign(s->h_shift, s->h_shift + 3 * (size_t)n);
-        for (int r = 0; r < n; ++r) {
+        if (j->perm.empty()) {
+          j->out_score.assign(s->h_score, s->h_score + n);
+          j->out_shift.assign(s->h_shift, s->h_shift + 3 * (size_t)n);
+        } else {                              // back to submission order
+          j->out_score.assign((size_t)j->R, -INFINITY);
+          j->out_shift.assign(3 * (size_t)j->R, 0);
+          for (int i = 0; i < n; ++i) {
+            const int r = j->perm[i];
+            j->out_score[r] = s->h_score[i];
+            for (int a = 0; a < 3; ++a) j->out_shift[3 * (size_t)r + a] = s->h_shift[3 * (size_t)i + a];
+          }
+        }
+        for (int r = 0; r < (int)j->out_score.size(); ++r) {
           const float v = j->out_score[r];
           if (std::isfinite(v) && (j->best_index < 0 || v > j->best)) {
             j->best = v;
@@ -508,16 +535,19 @@ cs_ngf_status cs_ngf_server_wait(cs_ngf_server* sv, int64_t job_id, double timeo
   std::memset(res, 0, sizeof(*res));
   res->status = j->status;
   res->rotations = j->R;
-  res->scored = (int32_t)j->out_score.size();
+  res->scored = (int32_t)j->cursor;
   res->score = j->best;
   res->rot_index = j->best_index;
   for (int a = 0; a < 3; ++a) res->shift[a] = j->best_shift[a];
   res->latency_ms = ms_between(j->t_submit, j->t_done);
   res->queue_ms = j->was_admitted ? ms_between(j->t_submit, j->t_admit) : res->latency_ms;
-  if (best_score && !j->out_score.empty())
-    std::memcpy(best_score, j->out_score.data(), sizeof(float) * j->out_score.size());
-  if (best_shift && !j->out_shift.empty())
-    std::memcpy(best_shift, j->out_shift.data(), sizeof(int32_t) * j->out_shift.size());
+  // every rotation: its result, or -inf / (0, 0, 0) if it was not scored
+  for (int r = 0; r < j->R; ++r) {
+    const bool have = (size_t)r < j->out_score.size();
+    if (best_score) best_score[r] = have ? j->out_score[r] : -INFINITY;
+    if (best_shift)
+      for (int a = 0; a < 3; ++a) best_shift[3 * (size_t)r + a] = have ? j->out_shift[3 * (size_t)r + a] : 0;
+  }
   const cs_ngf_status st = j->status;
   if (st) fail(st, j->error);
   sv->jobs.erase(it);

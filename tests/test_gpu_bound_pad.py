@@ -167,3 +167,67 @@ def test_no_admitted_shift_anywhere(cs):
     sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(zero), p.quats)]
     assert np.all(np.isneginf(sc)) and np.all(sh == 0)
     assert all(v >= n for v, n in zip(f.pad, p.A.shape))
+
+
+def rotation_lengths(p, q, gamma=0.5):
+    _, Mh = O.resample(p.B, p.MB, q)
+    rg = admitted_range(p.MA, Mh, gamma)
+    if any(r is None for r in rg):
+        return None
+    return tuple(min(v for v in PADS if v >= n + max(-lo, hi)) for n, (lo, hi) in zip(p.A.shape, rg))
+
+
+def length_classes(per, class_cost=4.0, max_classes=8):
+    """The library's grouping rule: rotations needing the same lengths form a
+    class; the cheapest pair merges (lengths raised to cover both) while the
+    added transform volume is below class_cost rotations of the smaller one,
+    or while there are more than max_classes."""
+    cls = {}
+    for r, t in enumerate(per):
+        if t is not None:
+            cls.setdefault(t, []).append(r)
+    cls = [[list(k), v] for k, v in cls.items()]
+    vol = lambda t: t[0] * t[1] * t[2]
+    while len(cls) > 1:
+        best = None
+        for c in range(len(cls)):
+            for d in range(c + 1, len(cls)):
+                m = [max(a, b) for a, b in zip(cls[c][0], cls[d][0])]
+                cost = (vol(m) - vol(cls[c][0])) * len(cls[c][1]) + (vol(m) - vol(cls[d][0])) * len(cls[d][1])
+                if best is None or cost < best[0]:
+                    best = (cost, c, d, m)
+        cost, c, d, m = best
+        if cost >= class_cost * min(vol(cls[c][0]), vol(cls[d][0])) and len(cls) <= max_classes:
+            break
+        cls[c][0] = m
+        cls[c][1] += cls[d][1]
+        del cls[d]
+    return cls
+
+
+def test_rotations_grouped_by_their_own_lengths(cs):
+    """Each rotation gets the lengths its own admitted shifts need; the call
+    scores the classes one after another and returns the results in the
+    caller's order.  Every rotation is checked against the oracle, and the
+    whole set against the full-length mode."""
+    p = synth.small_pair(21, (30, 30, 30), masks="threshold", n_rot=48)
+    per = [rotation_lengths(p, q) for q in p.quats]
+    cls = length_classes(per)
+    assert len(cls) > 2
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), batch=4)
+    sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+    assert f.length_sets == len(cls)
+    assert f.pad in {tuple(c[0]) for c in cls}
+    for r, q in enumerate(p.quats):
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q)
+        check_best_against_map(omap, sc[r], sh[r])
+    ff = cs.prepare_fixed(dev(p.A), dev(p.MA), batch=4, pad_mode="full")
+    sf, cf = [t.cpu().numpy() for t in ff.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+    fin = np.isfinite(sf)
+    np.testing.assert_array_equal(np.isfinite(sc), fin)
+    assert np.max(np.abs(sc[fin] - sf[fin])) <= 1e-4 * np.max(np.abs(sf[fin]))
+    # a second call with the rotations in reverse order gives the same per-rotation results
+    sr, cr = [t.cpu().numpy()[::-1] for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats[::-1])]
+    np.testing.assert_allclose(sr, sc, rtol=0, atol=1e-4 * np.max(np.abs(sf[fin])))
+    s, ri, chi = f.align(dev(p.B), dev(p.MB), p.quats)
+    assert ri == int(np.argmax(sc)) and chi == tuple(int(v) for v in sh[ri])
