@@ -71,12 +71,18 @@ __device__ __forceinline__ uint8_t mask_voxel(const uint8_t* __restrict__ MB, co
   AxisSample ax, ay, az;
   sample_axes(R, g, x, y, z, ax, ay, az);
   if (!(ax.inside && ay.inside && az.inside)) return 0;
-  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-  const long long b000 = (long long)az.i0 * sz + (long long)ay.i0 * sy + ax.i0;
-  const long long o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+  const int sy = g.nx, sz = g.nx * g.ny;          // volumes hold < 2^31 voxels
+  const int b000 = az.i0 * sz + ay.i0 * sy + ax.i0;
+  const int o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+  unsigned bits = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) bits |= (__ldg(&MB[b000 + o[k]]) ? 1u : 0u) << k;
+  // equal corners: every lerp a + t (a - a) returns a exactly
+  if (bits == 0u) return 0;
+  if (bits == 0xffu) return 1;
   float c[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) c[k] = __ldg(&MB[b000 + o[k]]) ? 1.0f : 0.0f;
+  for (int k = 0; k < 8; ++k) c[k] = ((bits >> k) & 1u) ? 1.0f : 0.0f;
   float m00 = lerp_rn(c[0], c[1], ax.t), m01 = lerp_rn(c[2], c[3], ax.t);
   float m10 = lerp_rn(c[4], c[5], ax.t), m11 = lerp_rn(c[6], c[7], ax.t);
   float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
