@@ -325,7 +325,6 @@ def run_ours(args):
     for _ in range(args.warmup):
         res = step()
     torch.cuda.synchronize()
-    pad = f.pad                                     # FFT lengths the calls use
 
     def barrier():
         if ws > 1:
@@ -401,15 +400,16 @@ def run_ours(args):
     h2d = 2 * nvox * 5 + R * 36
     d2h = R * 16 + 4
 
-    # ---------------- roofline of the dominant kernel
+    # ---------------- roofline of the dominant kernel: the model bytes (and
+    # flops) of every launch of the profiled step, per class of FFT lengths
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v[0] for k, v in stages.items()}
     dom = max(("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x"), key=lambda k: stage_ms[k])
-    nbatches = -(-R // f.batch)
-    total_bytes = 0
-    for b in range(nbatches):
-        nb = min(f.batch, R - b * f.batch)
-        total_bytes += stage_bytes(dims, pad, nb, dom, precision=args.precision)
+    classes = f.length_classes()
+    launches_of = [(cp, min(f.batch, cnt - b * f.batch)) for cp, cnt in classes
+                   for b in range(-(-cnt // f.batch))]
+    nbatches = len(launches_of)
+    total_bytes = sum(stage_bytes(dims, cp, nb, dom, precision=args.precision) for cp, nb in launches_of)
     total_bytes *= prof_steps
     achieved = total_bytes / (stage_ms[dom] / 1000.0) / 1e9 if stage_ms[dom] > 0 else 0.0
     tr = ncu_traffic(dom, args.precision)
@@ -423,7 +423,7 @@ def run_ours(args):
 
     roofline_alu = None
     if dom == "zmac":
-        fl = sum(zmac_flops(dims, pad, min(f.batch, R - b * f.batch)) for b in range(nbatches)) * prof_steps
+        fl = sum(zmac_flops(dims, cp, nb) for cp, nb in launches_of) * prof_steps
         ach = fl / (stage_ms[dom] / 1000.0) / 1e12 if stage_ms[dom] > 0 else 0.0
         roofline_alu = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": ach / FP32_ALU_PEAK_TFLOPS, "kernel": dom,
@@ -446,8 +446,10 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f32 arithmetic, bf16 channel intermediates",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", "BF16 form"), "volume": list(dims), "fft": list(pad),
+            "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", "BF16 form"), "volume": list(dims),
+                       "fft": list(max(classes, key=lambda c: c[1])[0]),
                        "padding": PADDING[args.pad_mode], "fft_full_linear": list(f.max_pad),
+                       "fft_classes": [{"fft": list(cp), "rotations": n} for cp, n in classes],
                        "rotations_per_gpu": R, "batch": f.batch, "masks": "thresholded foreground",
                        "l2": "inputs larger than L2: every step streams >1 TB of FFT intermediates",
                        "step": "update_fixed + score all rotations + max over rotations"},
@@ -523,7 +525,9 @@ def run_large(args):
     print(json.dumps({
         "metric": "256^3 rotations/s (all-shift maps, 512^3 FFT)", "unit": UNIT, "value": R / dt,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"256^3 pair, {R} rotations", "fft": list(f.pad), "batch": f.batch,
+        "config": {"workload": f"256^3 pair, {R} rotations",
+                   "fft_classes": [{"fft": list(cp), "rotations": n} for cp, n in f.length_classes()],
+                   "batch": f.batch,
                    "device_bytes": f.fixed_bytes + f.workspace_bytes},
         "seconds": dt,
         "result": {"best_rotation": res[1], "shift": list(res[2]), "score": res[0],

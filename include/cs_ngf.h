@@ -106,7 +106,9 @@ typedef struct {
   float eps;         /* Eq. 1 regulariser; the paper uses 1e-5 */
   float gamma;       /* minimum overlap fraction in (0, 1]; the paper uses 0.5 */
   int32_t pad[3];    /* FFT lengths (z, y, x); 0 = automatic */
-  int32_t batch;     /* rotations per launch group; 0 = automatic (memory-sized);
+  int32_t batch;     /* rotations per launch group; 0 = automatic (memory-sized, at
+                        most 32); a value above 65535 / (fields x nz) is lowered to
+                        that (4 fields for the squared measure, 3 unsquared);
                         an odd value above 1 is rounded down to even, since the
                         masks of rotations 2k and 2k+1 share one transform.
                         Results are bit-identical for every even batch; with
@@ -375,6 +377,13 @@ cs_ngf_status cs_ngf_global_align(const float* A, const uint8_t* maskA, const fl
 
 /* Sizes and FFT lengths of a handle.  info: host. */
 cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info);
+
+/* The sets of FFT lengths the last scoring call used (bound-limited padding
+ * groups rotations by the lengths they need; one set otherwise), in the order
+ * they were scored.  Fills up to cap entries of host pads [cap][3] (z, y, x)
+ * and counts [cap] (rotations scored with those lengths; either may be NULL)
+ * and returns the number of sets (0 for a NULL handle or before any call). */
+int32_t cs_ngf_length_sets(const cs_ngf_fixed* f, int32_t cap, int32_t* pads, int32_t* counts);
 
 /* Free every device allocation of the handle (NULL is a no-op).  The caller
  * makes sure no work that uses the handle is still in flight. */

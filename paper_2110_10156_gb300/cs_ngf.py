@@ -31,7 +31,7 @@ EXPORTED = (
     "cs_ngf_launch_count", "cs_ngf_score_rotations_noalloc",
     "cs_ngf_server_default_config", "cs_ngf_server_create", "cs_ngf_server_submit",
     "cs_ngf_server_cancel", "cs_ngf_server_wait", "cs_ngf_server_stats", "cs_ngf_server_destroy",
-    "cs_ngf_search_default_config", "cs_ngf_global_align",
+    "cs_ngf_search_default_config", "cs_ngf_global_align", "cs_ngf_length_sets",
 )
 
 MAX_LEVELS = 8
@@ -105,6 +105,8 @@ _lib.cs_ngf_status_string.argtypes = [_i32]
 _lib.cs_ngf_status_string.restype = ctypes.c_char_p
 _lib.cs_ngf_last_error.argtypes = []
 _lib.cs_ngf_last_error.restype = ctypes.c_char_p
+_lib.cs_ngf_length_sets.argtypes = [ctypes.c_void_p, _i32, ctypes.c_void_p, ctypes.c_void_p]
+_lib.cs_ngf_length_sets.restype = _i32
 _lib.cs_ngf_auto_pad.argtypes = [_i32]
 _lib.cs_ngf_auto_pad.restype = _i32
 _lib.cs_ngf_update_fixed.argtypes = [_vp, _vp, _vp, _vp]
@@ -238,6 +240,14 @@ class Fixed:
         """FFT lengths (z, y, x) in use: those of the last call (bound-limited
         padding may shorten them below max_pad)."""
         return tuple(self._info().pad)
+
+    def length_classes(self):
+        """[((Pz, Py, Px), rotations)] of the last scoring call, in the order scored."""
+        n = int(_lib.cs_ngf_length_sets(self._h, 0, None, None))
+        pads = (ctypes.c_int32 * (3 * max(n, 1)))()
+        counts = (ctypes.c_int32 * max(n, 1))()
+        _lib.cs_ngf_length_sets(self._h, n, pads, counts)
+        return [((pads[3 * c], pads[3 * c + 1], pads[3 * c + 2]), int(counts[c])) for c in range(n)]
 
     @property
     def length_sets(self):

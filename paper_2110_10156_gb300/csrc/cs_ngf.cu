@@ -579,18 +579,23 @@ cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream
   ends.assign(1, R);
   pads.assign({f->g.Pz, f->g.Py, f->g.Px});
   f->length_sets = 1;
+  f->last_pads = pads;
+  f->last_counts.assign(1, R);
   if (f->pad_mode != CS_NGF_PAD_BOUND) return CS_NGF_OK;
   if (cs_ngf_status s = rotation_bounds(f, MB, R, st)) return s;
   std::vector<LengthClass> cls = length_classes(f, R);
   f->length_sets = (int)cls.size();
   ends.clear();
   pads.clear();
+  f->last_counts.clear();
   int k = 0;
   for (const auto& c : cls) {
     k += (int)c.rot.size();
     ends.push_back(k);
     pads.insert(pads.end(), c.pad, c.pad + 3);
+    f->last_counts.push_back((int)c.rot.size());
   }
+  f->last_pads = pads;
   if (cls.size() == 1) return CS_NGF_OK;
   // the stream is idle (rotation_bounds waited for it): rot_h is free
   std::vector<RotMat> orig(f->rot_h, f->rot_h + R);
@@ -798,6 +803,9 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
     const size_t budget = free_b > uv_elems * sizeof(float2) ? (free_b - uv_elems * sizeof(float2)) / 3 : 0;
     batch = (int)std::max<size_t>(1, std::min<size_t>(32, budget / per_rot));
   }
+  // launch grids index (rotation, field, z-plane) and (rotation, shift plane)
+  // in their y dimension, at most 65535 blocks
+  batch = std::min(batch, 65535 / std::max(g.nf * g.nz, 2 * g.nz - 1));
   // the masks of rotations 2k and 2k+1 share one transform; an even batch
   // keeps every pair inside one launch group, so results do not depend on it
   if (batch > 1 && (batch & 1)) --batch;
@@ -955,6 +963,17 @@ cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info) {
 }
 
 void cs_ngf_release(cs_ngf_fixed* f) { free_handle(f); }
+
+int32_t cs_ngf_length_sets(const cs_ngf_fixed* f, int32_t cap, int32_t* pads, int32_t* counts) {
+  if (!f) return 0;
+  const int n = (int)f->last_counts.size();
+  for (int c = 0; c < n && c < cap; ++c) {
+    if (pads)
+      for (int a = 0; a < 3; ++a) pads[3 * c + a] = f->last_pads[3 * (size_t)c + a];
+    if (counts) counts[c] = f->last_counts[c];
+  }
+  return n;
+}
 
 cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* maskA, void* stream) {
   g_last_error.clear();

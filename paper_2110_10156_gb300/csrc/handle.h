@@ -34,6 +34,8 @@ struct cs_ngf_fixed {
   int32_t* perm_shift = nullptr;
   int allb_cap = 0;
   int length_sets = 1;         // sets of FFT lengths the last scoring call used
+  std::vector<int> last_pads;  // their lengths [3 per set] and rotation counts
+  std::vector<int> last_counts;
   // one captured graph per set of FFT lengths (all reference the same buffers)
   struct GraphSlot { int pad[3]; cudaGraphExec_t exec; };
   std::vector<GraphSlot> graphs;

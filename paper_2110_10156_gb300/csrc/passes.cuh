@@ -235,13 +235,15 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
   extern __shared__ float2 ex[];
   const int t = threadIdx.x;
-  const long long plane = blockIdx.x;                // ((r * nf) + j) * nz + z
+  // kx tiles run fastest over the grid, so the blocks that read the two halves
+  // of a 128-byte line of F0 run together and the second one hits in L2
+  const long long plane = blockIdx.y;                // ((r * nf) + j) * nz + z
   const long long rj = plane / g.nz;
   const int z = (int)(plane - rj * g.nz);
   const int r = (int)(rj / g.nf), j = (int)(rj - (long long)r * g.nf);
   const bool is_mask = j == g.nch;
   if (is_mask && (r & 1)) return;                    // paired into the even rotation's mask field
-  const int kx0 = blockIdx.y * W;
+  const int kx0 = blockIdx.x * W;
   {
     const int col = t % W, n2 = t / W;
     const int kx = kx0 + col;
@@ -289,7 +291,7 @@ template <int P>
 void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, cudaStream_t st) {
   constexpr int W = FwdYCfg<P>::W, N2 = Split<P>::N2;
   const size_t smem = FwdYCfg<P>::smem_bytes;
-  dim3 grid((unsigned)(nrot * g.nf * g.nz), (unsigned)((g.Px + W - 1) / W));
+  dim3 grid((unsigned)((g.Px + W - 1) / W), (unsigned)(nrot * g.nf * g.nz));   // y: at most 32 * 4 * 256
   auto go = [&](auto kern) {
     set_smem(kern, smem);
     kern<<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
