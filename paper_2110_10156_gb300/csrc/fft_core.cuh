@@ -223,7 +223,7 @@ template <> struct Split<80>  { static constexpr int N1 = 8,  N2 = 10; };
 template <> struct Split<100> { static constexpr int N1 = 10, N2 = 10; };
 template <> struct Split<128> { static constexpr int N1 = 8,  N2 = 16; };
 template <> struct Split<160> { static constexpr int N1 = 8,  N2 = 20; };
-template <> struct Split<200> { static constexpr int N1 = 8,  N2 = 25; };
+template <> struct Split<200> { static constexpr int N1 = 10, N2 = 20; };
 template <> struct Split<256> { static constexpr int N1 = 16, N2 = 16; };
 template <> struct Split<320> { static constexpr int N1 = 16, N2 = 20; };
 template <> struct Split<400> { static constexpr int N1 = 16, N2 = 25; };
