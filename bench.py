@@ -138,7 +138,7 @@ def stage_bytes(dims, pad, nb, stage, nch=3, precision="fp32"):
     Pz, Py, Px = pad
     vz, vy = 2 * nz - 1, 2 * ny - 1
     nvox = nz * ny * nx
-    cb = 4 if precision == "bf16" else 8
+    cb = 8 if precision == "fp32" else 4
     per_elem = nch * nb * cb + ((nb + 1) // 2) * 8     # bytes per element position, all fields
     F0 = per_elem * nz * ny * Px
     F1 = per_elem * nz * Px * Py
@@ -444,9 +444,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f32 arithmetic, bf16 channel intermediates",
+            "dtype": "f32" if args.precision == "fp32" else f"f32 arithmetic, {args.precision} channel intermediates",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", "BF16 form"), "volume": list(dims),
+            "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", f"{args.precision.upper()} form"), "volume": list(dims),
                        "fft": list(max(classes, key=lambda c: c[1])[0]),
                        "padding": PADDING[args.pad_mode], "fft_full_linear": list(f.max_pad),
                        "fft_classes": [{"fft": list(cp), "rotations": n} for cp, n in classes],
@@ -689,7 +689,7 @@ def main():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--rotations", type=int, default=1000)
     ap.add_argument("--batch", type=int, default=0)
-    ap.add_argument("--precision", choices=("fp32", "bf16"), default="fp32")
+    ap.add_argument("--precision", choices=("fp32", "bf16", "fp16"), default="fp32")
     ap.add_argument("--pad-mode", choices=("bound", "full"), default="bound")
     ap.add_argument("--ref-sample", type=int, default=16,
                     help="oracle rotations per CPU step (at most one per core)")

@@ -73,8 +73,13 @@ typedef enum {
 
 typedef enum {
   CS_NGF_FP32 = 0,  /* all intermediates FP32 */
-  CS_NGF_BF16 = 1   /* NGF channel intermediates of the forward x and y passes stored as
+  CS_NGF_BF16 = 1,  /* NGF channel intermediates of the forward x and y passes stored as
                        BF16 (FP32 arithmetic); the mask / overlap count path stays FP32 */
+  CS_NGF_FP16 = 2   /* the same intermediates stored as FP16 (3 more mantissa bits than
+                       BF16, range to 65504): each channel field is scaled by a power of
+                       two chosen from its magnitude bound (at most 1 per voxel, times the
+                       voxels summed by each transform) to stay below 2^15; the scale is
+                       exact and undone on load */
 } cs_ngf_precision;
 
 /* FFT lengths per call.  A circular correlation of length P holds at slot

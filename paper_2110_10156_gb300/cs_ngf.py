@@ -46,7 +46,7 @@ class Config(ctypes.Structure):
 
 
 MEASURES = {"squared": 0, "unsquared": 1}
-PRECISIONS = {"fp32": 0, "bf16": 1}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 PAD_MODES = {"full": 0, "bound": 1}
 
 

@@ -348,7 +348,8 @@ cs_ngf_status ensure_graph(cs_ngf_fixed* f) {
 // Section 3.1 A side: NGF channels of A times M_A, forward FFTs, weights -> f->UV
 cs_ngf_status run_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* MA, cudaStream_t st) {
   Geo g = f->g;
-  g.bf16 = 0;                     // the fixed spectra are always computed in FP32
+  g.store = kStoreF32;            // the fixed spectra are always computed in FP32
+  for (int j = 0; j < 4; ++j) g.scale0[j] = g.scale1[j] = 1.0f;
   { Stage sp(f, 6, st); k_copy_in<<<1024, 256, 0, st>>>(A, MA, g.nvox, f->Bh, f->Mh); }
   if (cs_ngf_status s = check_launch("copy_in")) return s;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
@@ -400,6 +401,23 @@ cs_ngf_status set_pads(cs_ngf_fixed* f, const int pad[3], cudaStream_t st) {
   g.Py = pad[1];
   g.Px = pad[2];
   return run_fixed(f, f->A_keep, f->MA_keep, st);
+}
+
+// FP16 form: per channel field, the power of two that keeps the field's
+// magnitude bound at most 2^15 (half of FP16's range) after the x pass
+// (scale0) and after the y pass (scale1).  Per voxel a packed field has
+// modulus at most 1 ((xx, yy), (zz, xy); Eq. 3's (x, y), (z, 0)) or 1/2
+// ((xz, yz)), as the NGF is a unit vector or shorter (Eq. 1); a transform
+// along an axis of n voxels multiplies the bound by at most n.
+void set_field_scales(Geo& g) {
+  for (int j = 0; j < 4; ++j) g.scale0[j] = g.scale1[j] = 1.0f;
+  if (g.store != kStoreF16) return;
+  for (int j = 0; j < g.nch; ++j) {
+    const double b = (g.nch == 3 && j == 2) ? 0.5 : 1.0;
+    const double b0 = b * g.nx, b1 = b * g.nx * (double)g.ny;
+    g.scale0[j] = (float)std::ldexp(1.0, -std::max(0, (int)std::ceil(std::log2(b0 / 32768.0))));
+    g.scale1[j] = (float)std::ldexp(1.0, -std::max(0, (int)std::ceil(std::log2(b1 / 32768.0))));
+  }
 }
 
 // the shortest supported length >= need, at most cap
@@ -643,7 +661,7 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
   if (cfg.batch < 0) return fail(CS_NGF_EINVAL, "batch must be >= 0");
   if (cfg.measure != CS_NGF_SQUARED && cfg.measure != CS_NGF_UNSQUARED)
     return fail(CS_NGF_EINVAL, "unknown measure");
-  if (cfg.precision != CS_NGF_FP32 && cfg.precision != CS_NGF_BF16)
+  if (cfg.precision != CS_NGF_FP32 && cfg.precision != CS_NGF_BF16 && cfg.precision != CS_NGF_FP16)
     return fail(CS_NGF_EINVAL, "unknown precision");
   if (cfg.pad_mode != CS_NGF_PAD_FULL && cfg.pad_mode != CS_NGF_PAD_BOUND)
     return fail(CS_NGF_EINVAL, "unknown pad_mode");
@@ -670,7 +688,7 @@ Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure, int precis
   const size_t Pz = pad[0], Py = pad[1], Px = pad[2];
   const size_t vz = 2 * nz - 1, vy = 2 * ny - 1, nvox = nz * ny * nx;
   const size_t nch = channel_fields(measure), nf = nch + 1;
-  const size_t cb = precision == CS_NGF_BF16 ? 4 : 8;            // bytes per channel value
+  const size_t cb = precision == CS_NGF_FP32 ? 8 : 4;            // bytes per channel value
   const size_t E0 = nz * ny * Px, E1 = nz * Px * Py;               // values per field of F0, F1
   Sizes z;
   z.f02_elems = (std::max((nch * cb + 8) * E0, vz * Px * Py * 8) + 7) / 8;
@@ -788,7 +806,8 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   g.nvox = (long long)g.nz * g.ny * g.nx;
   g.nch = channel_fields(cfg.measure);
   g.nf = g.nch + 1;
-  g.bf16 = cfg.precision == CS_NGF_BF16 ? 1 : 0;
+  g.store = cfg.precision == CS_NGF_BF16 ? kStoreBF16 : cfg.precision == CS_NGF_FP16 ? kStoreF16 : kStoreF32;
+  set_field_scales(g);
   for (int a = 0; a < 3; ++a) f->alloc_pad[a] = pad[a];
   f->pad_mode = cfg.pad_mode;
 

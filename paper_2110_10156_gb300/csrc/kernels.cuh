@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "fft_core.cuh"
 
@@ -40,16 +41,24 @@ struct Geo {
   long long nvox;       // nz*ny*nx
   int nch;              // packed channel fields: 3 (Eq. 2, squared) or 2 (Eq. 3, unsquared)
   int nf;               // fields per rotation: nch + 1 (the mask field is last)
-  int bf16;             // channel fields of F0 / F1 stored as BF16 pairs (reduced-precision form)
+  int store;            // channel fields of F0 / F1: kStoreF32, kStoreBF16 or kStoreF16
+  // FP16 form: channel field j of F0 (F1) is stored as its value times
+  // scale0[j] (scale1[j]), a power of two that keeps it inside FP16's range;
+  // 1 in the other forms and for the mask field (j = nch)
+  float scale0[4], scale1[4];
 };
 
+constexpr int kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2;
+
 // Storage of the packed fields of F0 / F1 for a batch of rotations: the
-// channel fields j < nch hold FP32 complex values, or BF16 pairs in the
-// reduced-precision form; the mask field j = nch is always FP32 complex, so
-// the overlap count N(chi) keeps FP32 accuracy.  E = complex values per field.
-template <bool BF>
+// channel fields j < nch hold FP32 complex values, or 16-bit pairs in the
+// reduced-precision forms (BF16; FP16 with a per-field power-of-two scale);
+// the mask field j = nch is always FP32 complex, so the overlap count N(chi)
+// keeps FP32 accuracy.  E = complex values per field.  put and get take and
+// return the field's true values; the FP16 scale is applied inside.
+template <int ST>
 struct Fields {
-  static constexpr int CB = BF ? 4 : 8;   // bytes per channel-field value
+  static constexpr int CB = ST == kStoreF32 ? 8 : 4;   // bytes per channel-field value
   __host__ __device__ static long long rot_bytes(const Geo& g, long long E) {
     return (long long)g.nch * E * CB + E * 8;
   }
@@ -60,12 +69,20 @@ struct Fields {
                                                       int r, int j) {
     return (const char*)base + (long long)r * rot_bytes(g, E) + (long long)j * E * CB;
   }
-  __device__ __forceinline__ static void put(char* f, long long i, float2 v, bool mask) {
-    if (BF && !mask) reinterpret_cast<__nv_bfloat162*>(f)[i] = __float22bfloat162_rn(v);
+  // scale: the field's storage scale (FP16 form; ignored otherwise)
+  __device__ __forceinline__ static void put(char* f, long long i, float2 v, bool mask, float scale) {
+    if (ST == kStoreBF16 && !mask) reinterpret_cast<__nv_bfloat162*>(f)[i] = __float22bfloat162_rn(v);
+    else if (ST == kStoreF16 && !mask)
+      reinterpret_cast<__half2*>(f)[i] = __float22half2_rn(make_float2(v.x * scale, v.y * scale));
     else reinterpret_cast<float2*>(f)[i] = v;
   }
-  __device__ __forceinline__ static float2 get(const char* f, long long i, bool mask) {
-    if (BF && !mask) return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(f)[i]);
+  // inv_scale: 1 / the field's storage scale (FP16 form; ignored otherwise)
+  __device__ __forceinline__ static float2 get(const char* f, long long i, bool mask, float inv_scale) {
+    if (ST == kStoreBF16 && !mask) return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(f)[i]);
+    if (ST == kStoreF16 && !mask) {
+      const float2 v = __half22float2(reinterpret_cast<const __half2*>(f)[i]);
+      return make_float2(v.x * inv_scale, v.y * inv_scale);
+    }
     return reinterpret_cast<const float2*>(f)[i];
   }
 };
@@ -138,7 +155,7 @@ __global__ void k_copy_in(const float* __restrict__ A, const uint8_t* __restrict
                           long long n, float* __restrict__ Bh, uint8_t* __restrict__ Mh);
 
 // ----------------------------------------------------------------- FFT passes
-// F0 / F1 are laid out by Fields<g.bf16> (FP32 everywhere when g.bf16 == 0)
+// F0 / F1 are laid out by Fields<g.store> (FP32 everywhere when g.store == kStoreF32)
 template <int P> void launch_fwd_x(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw,
                                    Geo g, int nrot, cudaStream_t st);
 template <int P> void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot,

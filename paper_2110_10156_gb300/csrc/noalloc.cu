@@ -203,6 +203,8 @@ extern "C" cs_ngf_status cs_ngf_score_rotations_noalloc(
   g.nvox = (long long)g.nz * g.ny * g.nx;
   g.nch = 3;                         // Eq. 2 (squared) measure
   g.nf = 4;
+  g.store = kStoreF32;
+  for (int j = 0; j < 4; ++j) g.scale0[j] = g.scale1[j] = 1.0f;
 
   float2* UV = (float2*)(base + kOffUV);
   float2* F02 = (float2*)(base + kOffF02);

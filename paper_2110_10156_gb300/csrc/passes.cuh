@@ -35,6 +35,14 @@ struct FwdIn {
   }
 };
 
+// calls f with the storage form of the channel fields as a compile-time constant
+template <class F>
+static void by_store(int store, F&& f) {
+  if (store == kStoreBF16) f(std::integral_constant<int, kStoreBF16>{});
+  else if (store == kStoreF16) f(std::integral_constant<int, kStoreF16>{});
+  else f(std::integral_constant<int, kStoreF32>{});
+}
+
 template <class K>
 static void set_smem(K kern, size_t bytes) {
   if (bytes > 48 * 1024)
@@ -58,7 +66,7 @@ struct FwdXCfg {
   static constexpr size_t smem_bytes = ex_bytes + (HALF ? 0 : (size_t)NI * NT * sizeof(float4));
 };
 
-template <int P, int ROWS, bool BF, bool HALF>
+template <int P, int ROWS, int ST, bool HALF>
 __global__ void __launch_bounds__(ROWS * Split<P>::N2, 2)
 k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __restrict__ F0,
         const float2* __restrict__ tw, Geo g, long long nrows) {
@@ -161,14 +169,15 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
         const long long rz2 = gr / g.ny;
         const int y2 = (int)(gr - rz2 * g.ny);
         const int r2 = (int)(rz2 / g.nz), z2 = (int)(rz2 - (long long)r2 * g.nz);
-        char* fld = Fields<BF>::field(F0, g, rows_per_field * P, r2, j);
+        char* fld = Fields<ST>::field(F0, g, rows_per_field * P, r2, j);
         const long long row = ((long long)z2 * g.ny + y2) * P;
+        const float sc = g.scale0[j];
         if (j == g.nch) {
 #pragma unroll
-          for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(fld, row + k1 + N1 * k2, u[k2], true);
+          for (int k2 = 0; k2 < N2; ++k2) Fields<ST>::put(fld, row + k1 + N1 * k2, u[k2], true, sc);
         } else {
 #pragma unroll
-          for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(fld, row + k1 + N1 * k2, u[k2], false);
+          for (int k2 = 0; k2 < N2; ++k2) Fields<ST>::put(fld, row + k1 + N1 * k2, u[k2], false, sc);
         }
       }
     }
@@ -188,8 +197,7 @@ void launch_fwd_x_t(const float* Bh, const uint8_t* Mh, void* F0, const float2* 
     set_smem(kern, smem);
     kern<<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
   };
-  if (g.bf16) go(k_fwd_x<P, ROWS, true, HALF>);
-  else go(k_fwd_x<P, ROWS, false, HALF>);
+  by_store(g.store, [&](auto st) { go(k_fwd_x<P, ROWS, decltype(st)::value, HALF>); });
 }
 
 template <int P>
@@ -226,7 +234,7 @@ template <int P> struct FwdYCfg {
   static constexpr int MIN_BLOCKS = pass_blocks(NT, smem_bytes, Split<P>::N2 > 20 ? 80 : 48);
 };
 
-template <int P, int W, bool BF, bool HALF>
+template <int P, int W, int ST, bool HALF>
 __global__ void __launch_bounds__(W * Split<P>::N2, FwdYCfg<P>::MIN_BLOCKS)
 k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __restrict__ tw,
         Geo g) {
@@ -247,21 +255,22 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
   {
     const int col = t % W, n2 = t / W;
     const int kx = kx0 + col;
-    const char* src = Fields<BF>::field(F0, g, (long long)g.nz * g.ny * g.Px, r, j);
+    const char* src = Fields<ST>::field(F0, g, (long long)g.nz * g.ny * g.Px, r, j);
+    const float isc = 1.0f / g.scale0[j];
     const long long zoff = (long long)z * g.ny * g.Px;
     float2 v[FI::NI];                     // y < ny: with ny <= P/2 the upper half is zero
     if (is_mask) {
 #pragma unroll
       for (int n1 = 0; n1 < FI::NI; ++n1) {
         const int y = N2 * n1 + n2;
-        v[n1] = (y < g.ny && kx < g.Px) ? Fields<BF>::get(src, zoff + (long long)y * g.Px + kx, true)
+        v[n1] = (y < g.ny && kx < g.Px) ? Fields<ST>::get(src, zoff + (long long)y * g.Px + kx, true, isc)
                                         : make_float2(0.f, 0.f);
       }
     } else {
 #pragma unroll
       for (int n1 = 0; n1 < FI::NI; ++n1) {
         const int y = N2 * n1 + n2;
-        v[n1] = (y < g.ny && kx < g.Px) ? Fields<BF>::get(src, zoff + (long long)y * g.Px + kx, false)
+        v[n1] = (y < g.ny && kx < g.Px) ? Fields<ST>::get(src, zoff + (long long)y * g.Px + kx, false, isc)
                                         : make_float2(0.f, 0.f);
       }
     }
@@ -274,14 +283,15 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
     if (kx < g.Px) {
       float2 u[N2];
       FS::template step2<-1>(u, ex + col * CS, k1);
-      char* dst = Fields<BF>::field(F1, g, (long long)g.nz * g.Px * P, r, j);
+      char* dst = Fields<ST>::field(F1, g, (long long)g.nz * g.Px * P, r, j);
       const long long row = ((long long)kx * g.nz + z) * P;       // [kx][z][ky]
+      const float sc = g.scale1[j];
       if (is_mask) {
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(dst, row + k1 + N1 * k2, u[k2], true);
+        for (int k2 = 0; k2 < N2; ++k2) Fields<ST>::put(dst, row + k1 + N1 * k2, u[k2], true, sc);
       } else {
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) Fields<BF>::put(dst, row + k1 + N1 * k2, u[k2], false);
+        for (int k2 = 0; k2 < N2; ++k2) Fields<ST>::put(dst, row + k1 + N1 * k2, u[k2], false, sc);
       }
     }
   }
@@ -297,8 +307,10 @@ void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, c
     kern<<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
   };
   const bool half = 2 * g.ny <= P;
-  if (g.bf16) half ? go(k_fwd_y<P, W, true, true>) : go(k_fwd_y<P, W, true, false>);
-  else half ? go(k_fwd_y<P, W, false, true>) : go(k_fwd_y<P, W, false, false>);
+  by_store(g.store, [&](auto st) {
+    constexpr int ST = decltype(st)::value;
+    half ? go(k_fwd_y<P, W, ST, true>) : go(k_fwd_y<P, W, ST, false>);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -350,7 +362,7 @@ struct ZmacCfg {
   static constexpr int MIN_BLOCKS = (fits2(smem_bytes) && regs_for(2) >= 128) ? 2 : 1;
 };
 
-template <int P, bool BF, bool HALF>
+template <int P, int ST, bool HALF>
 __global__ void __launch_bounds__(ZmacCfg<P, HALF>::NT, ZmacCfg<P, HALF>::MIN_BLOCKS)
 k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot, const int* __restrict__ bounds) {
@@ -402,8 +414,8 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   int pr = 0, pj = 0;                         // next field to copy
   auto fetch = [&](float2* buf) {             // copies field (pr, pj), if any, and advances
     if (pr < nrot) {
-      const char* src = Fields<BF>::field(F1, g, g.nz * plane_stride, pr, pj);
-      if (!BF || pj == g.nch) {
+      const char* src = Fields<ST>::field(F1, g, g.nz * plane_stride, pr, pj);
+      if (ST == kStoreF32 || pj == g.nch) {
 #pragma unroll
         for (int n1 = 0; n1 < H; ++n1) {
           const int z = N2 * n1 + n2;
@@ -426,13 +438,20 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   // recent copy group have landed
   auto take = [&](float2 (&v)[H], const float2* buf, int j) {
     cp_async_wait_one();
-    if (!BF || j == g.nch) {
+    if (ST == kStoreF32 || j == g.nch) {
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) v[n1] = buf[n1 * NT + t];
-    } else {
+    } else if (ST == kStoreBF16) {
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1)
         v[n1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(buf + n1 * NT + t));
+    } else {                                   // FP16: undo the field's power-of-two scale
+      const float isc = 1.0f / g.scale1[j];
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) {
+        const float2 h = __half22float2(*reinterpret_cast<const __half2*>(buf + n1 * NT + t));
+        v[n1] = make_float2(h.x * isc, h.y * isc);
+      }
     }
   };
   // the block's fixed-spectra tile: 7 contiguous runs of W*P values (rows
@@ -566,13 +585,11 @@ void launch_zmac_t(const void* F1, const float2* UV, float2* F2, const float2* t
                    const int* bounds, cudaStream_t st) {
   using C = ZmacCfg<P, HALF>;
   dim3 grid((unsigned)((g.Py + C::W - 1) / C::W), (unsigned)(g.Px / 2 + 1));
-  if (g.bf16) {
-    set_smem(k_zmac<P, true, HALF>, C::smem_bytes);
-    k_zmac<P, true, HALF><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
-  } else {
-    set_smem(k_zmac<P, false, HALF>, C::smem_bytes);
-    k_zmac<P, false, HALF><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
-  }
+  by_store(g.store, [&](auto sf) {
+    constexpr int ST = decltype(sf)::value;
+    set_smem(k_zmac<P, ST, HALF>, C::smem_bytes);
+    k_zmac<P, ST, HALF><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
+  });
 }
 
 template <int P>

@@ -42,7 +42,7 @@ def oracle150(pair150):
 
 
 @pytest.mark.parametrize("precision,tau,pad_mode", [("fp32", 1e-4, "bound"), ("bf16", 1e-2, "bound"),
-                                                    ("fp32", 1e-4, "full")])
+                                                    ("fp16", 1e-2, "bound"), ("fp32", 1e-4, "full")])
 def test_150_cubed_1000_rotations(cs, pair150, oracle150, precision, tau, pad_mode):
     p = pair150
     f = cs.prepare_fixed(dev(p.A), dev(p.MA), precision=precision, pad_mode=pad_mode)

@@ -275,3 +275,43 @@ def test_bf16_form_within_reduced_precision_tolerance(cs, dims, pad):
         omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad)
         check_best_against_map(omap, sc[r], sh[r], tau=TAU_BF16)
     assert worst > 0.0          # the reduced-precision path really differs from FP32 arithmetic
+
+
+# ------------------------------------------------------------ FP16 storage form
+@pytest.mark.parametrize("dims,pad", [((12, 10, 14), None), ((20, 17, 23), None), ((16, 15, 14), (320, 320, 320))])
+def test_fp16_form_within_reduced_precision_tolerance(cs, dims, pad):
+    """FP16 intermediates (per-field power-of-two scales): within the reduced
+    precision budget of the FP64 oracle, and closer to it than BF16."""
+    p = synth.small_pair(331 + sum(dims), dims, masks="threshold")
+    errs = {}
+    for prec in ("fp16", "bf16"):
+        f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=pad, precision=prec, pad_mode=pad_mode_for(pad))
+        worst = 0.0
+        for q in (IDENTITY, p.q_true, rand_quat(3)):
+            gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
+            omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad)
+            worst = max(worst, check_maps(omap, gmap, tau=TAU_BF16))
+        if prec == "fp16":
+            sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+            for r, q in enumerate(p.quats):
+                omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=pad)
+                check_best_against_map(omap, sc[r], sh[r], tau=TAU_BF16)
+        errs[prec] = worst
+        f.release()
+    assert 0.0 < errs["fp16"] < errs["bf16"]
+
+
+def test_fp16_form_scales_wide_planes(cs):
+    """Planes of 190 x 180 voxels: after the y pass a channel field can reach
+    about 34,000 per unit of NGF product, past half of FP16's range, so the
+    fields are stored at half scale.  The maps stay within the budget."""
+    p = synth.small_pair(707, (6, 190, 180), masks="threshold", n_rot=2)
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), precision="fp16")
+    g = cs.prepare_fixed(dev(p.A), dev(p.MA))
+    for q in (IDENTITY, p.q_true):
+        gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q)
+        check_maps(omap, gmap, tau=TAU_BF16)
+        fmap = g.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
+        fin = np.isfinite(fmap)
+        assert np.max(np.abs(gmap[fin] - fmap[fin])) <= 2e-3 * np.max(np.abs(fmap[fin]))
