@@ -310,7 +310,7 @@ def run_ours(args):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     A, MA, B, MB = dev(pair["A"]), dev(pair["MA"]), dev(pair["B"]), dev(pair["MB"])
     f = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=args.precision,
-                             pad_mode=args.pad_mode)
+                             pad_mode=args.pad_mode, autotune=args.autotune == "on")
     dims = f.dims
 
     def step():
@@ -450,6 +450,10 @@ def run_ours(args):
                        "fft": list(max(classes, key=lambda c: c[1])[0]),
                        "padding": PADDING[args.pad_mode], "fft_full_linear": list(f.max_pad),
                        "fft_classes": [{"fft": list(cp), "rotations": n} for cp, n in classes],
+                       "autotune": args.autotune == "on",
+                       "splits": [{"stage": e["stage"], "length": e["length"],
+                                   "split": list(e["splits"][e["variant"]]),
+                                   "ms": [round(v, 3) for v in e["ms"]]} for e in cs_ngf.tuning()],
                        "rotations_per_gpu": R, "batch": f.batch, "masks": "thresholded foreground",
                        "l2": "inputs larger than L2: every step streams >1 TB of FFT intermediates",
                        "step": "update_fixed + score all rotations + max over rotations"},
@@ -691,6 +695,9 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--precision", choices=("fp32", "bf16", "fp16"), default="fp32")
     ap.add_argument("--pad-mode", choices=("bound", "full"), default="bound")
+    ap.add_argument("--autotune", choices=("on", "off"), default="on",
+                    help="time both radix splits of each FFT pass on the first launch group "
+                         "at new lengths (warm-up) and keep the faster")
     ap.add_argument("--ref-sample", type=int, default=16,
                     help="oracle rotations per CPU step (at most one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

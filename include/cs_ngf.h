@@ -123,6 +123,14 @@ typedef struct {
   int32_t precision; /* cs_ngf_precision; default CS_NGF_FP32 */
   int32_t pad_mode;  /* cs_ngf_pad_mode; cs_ngf_default_config sets CS_NGF_PAD_BOUND.  The
                         lengths from pad (or automatic) are then the largest a call uses */
+  int32_t autotune;  /* 0 (default): every FFT pass uses its built-in radix split.
+                        1: the first launch group at a new set of FFT lengths times each
+                        pass with each split its length offers (e.g. 200 = 10 x 20 or
+                        8 x 25) and keeps the faster for the rest of the process
+                        (cs_ngf_tuning lists the choices).  Every split computes the same
+                        transform; results differ from the default only by FP32 rounding,
+                        and are reproducible within a process, not across processes
+                        whose timings choose differently. */
 } cs_ngf_config;
 
 typedef struct {
@@ -389,6 +397,24 @@ cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info);
  * and counts [cap] (rotations scored with those lengths; either may be NULL)
  * and returns the number of sets (0 for a NULL handle or before any call). */
 int32_t cs_ngf_length_sets(const cs_ngf_fixed* f, int32_t cap, int32_t* pads, int32_t* counts);
+
+/* Autotuning choices of this process (cs_ngf_config.autotune), one entry per
+ * FFT pass, length, input kind and storage form timed so far. */
+typedef struct {
+  int32_t pass;        /* 0 x forward, 1 y forward, 2 z forward + spectral sum + z inverse,
+                          3 y inverse, 4 x inverse */
+  int32_t length;      /* FFT length of the pass's axis */
+  int32_t half_input;  /* 1: the input fills at most half the length (pruned first stage) */
+  int32_t storage;     /* cs_ngf_precision of the channel fields it reads or writes */
+  int32_t variant;     /* the split chosen: 0 built-in, 1 alternative */
+  int32_t split[2][2]; /* (N1, N2) of each variant: length = N1 x N2 */
+  float ms[2];         /* the best time of each variant on the launch group it was timed on */
+} cs_ngf_tuning_entry;
+/* Fills up to cap entries of host out (may be NULL) and returns the number of
+ * entries.  cs_ngf_tuning_reset forgets them (handles keep the variants they
+ * hold until their lengths change). */
+int32_t cs_ngf_tuning(int32_t cap, cs_ngf_tuning_entry* out);
+void cs_ngf_tuning_reset(void);
 
 /* Free every device allocation of the handle (NULL is a no-op).  The caller
  * makes sure no work that uses the handle is still in flight. */

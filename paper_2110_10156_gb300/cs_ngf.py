@@ -32,6 +32,7 @@ EXPORTED = (
     "cs_ngf_server_default_config", "cs_ngf_server_create", "cs_ngf_server_submit",
     "cs_ngf_server_cancel", "cs_ngf_server_wait", "cs_ngf_server_stats", "cs_ngf_server_destroy",
     "cs_ngf_search_default_config", "cs_ngf_global_align", "cs_ngf_length_sets",
+    "cs_ngf_tuning", "cs_ngf_tuning_reset",
 )
 
 MAX_LEVELS = 8
@@ -42,7 +43,16 @@ STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "othe
 class Config(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32), ("measure", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("pad_mode", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("pad_mode", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+
+
+class TuningEntry(ctypes.Structure):
+    _fields_ = [("pass_", ctypes.c_int32), ("length", ctypes.c_int32), ("half_input", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("variant", ctypes.c_int32), ("split", (ctypes.c_int32 * 2) * 2),
+                ("ms", ctypes.c_float * 2)]
+
+
+PASS_NAMES = ("fwd_x", "fwd_y", "zmac", "inv_y", "inv_x")
 
 
 MEASURES = {"squared": 0, "unsquared": 1}
@@ -105,6 +115,10 @@ _lib.cs_ngf_status_string.argtypes = [_i32]
 _lib.cs_ngf_status_string.restype = ctypes.c_char_p
 _lib.cs_ngf_last_error.argtypes = []
 _lib.cs_ngf_last_error.restype = ctypes.c_char_p
+_lib.cs_ngf_tuning.argtypes = [_i32, ctypes.c_void_p]
+_lib.cs_ngf_tuning.restype = _i32
+_lib.cs_ngf_tuning_reset.argtypes = []
+_lib.cs_ngf_tuning_reset.restype = None
 _lib.cs_ngf_length_sets.argtypes = [ctypes.c_void_p, _i32, ctypes.c_void_p, ctypes.c_void_p]
 _lib.cs_ngf_length_sets.restype = _i32
 _lib.cs_ngf_auto_pad.argtypes = [_i32]
@@ -164,6 +178,23 @@ def launch_count() -> int:
     return int(_lib.cs_ngf_launch_count())
 
 
+def tuning():
+    """The process's autotuning choices (cs_ngf_tuning): one dict per FFT pass,
+    length, input kind and storage form timed so far."""
+    n = int(_lib.cs_ngf_tuning(0, None))
+    arr = (TuningEntry * max(n, 1))()
+    _lib.cs_ngf_tuning(n, arr)
+    store = {v: k for k, v in PRECISIONS.items()}
+    return [dict(stage=PASS_NAMES[e.pass_], length=e.length, half_input=bool(e.half_input),
+                 storage=store.get(e.storage, e.storage), variant=e.variant,
+                 splits=[tuple(e.split[v]) for v in range(2)], ms=[float(e.ms[0]), float(e.ms[1])])
+            for e in arr[:n]]
+
+
+def tuning_reset():
+    _lib.cs_ngf_tuning_reset()
+
+
 def auto_pad(n: int) -> int:
     return int(_lib.cs_ngf_auto_pad(int(n)))
 
@@ -194,7 +225,7 @@ class Fixed:
     """Handle on the device-resident fixed-volume spectra (cs_ngf_prepare_fixed)."""
 
     def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None,
-                 measure="squared", precision="fp32", pad_mode="bound"):
+                 measure="squared", precision="fp32", pad_mode="bound", autotune=False):
         import torch
         if A.dim() != 3:
             raise ValueError("A must be [nz][ny][nx]")
@@ -212,6 +243,7 @@ class Fixed:
         cfg.measure = MEASURES[measure]
         cfg.precision = PRECISIONS[precision]
         cfg.pad_mode = PAD_MODES[pad_mode]
+        cfg.autotune = 1 if autotune else 0
         self.measure = measure
         self.precision = precision
         self.pad_mode = pad_mode

@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/cs_ngf.h"
@@ -247,19 +250,147 @@ cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* quats, int R, cuda
   return CS_NGF_OK;
 }
 
-// the FFT passes for nb volumes already resampled into f->Bh / f->Mh
-cs_ngf_status run_transforms(cs_ngf_fixed* f, int nb, float* map, cudaStream_t st) {
+// ------------------------------------------------------------ autotuning
+// Process-wide choice of radix split per FFT pass, keyed by the pass, its
+// length, whether its input fills at most half the length, and the storage
+// form of the channel fields; with the best time of each variant.
+struct TuneKey {
+  int pass, P, half, store;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(pass, P, half, store) < std::tie(o.pass, o.P, o.half, o.store);
+  }
+};
+struct TuneVal { int variant; float ms[2]; };
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+constexpr int kPasses = 5;   // fwd_x, fwd_y, zmac, inv_y, inv_x
+
+// (N1, N2) of split variant v of length P; (0, 0) if P has no such variant
+template <int P>
+void split_into(int v, int32_t* n1, int32_t* n2) {
+  *n1 = *n2 = 0;
+  if constexpr (has_alt_split(P)) {
+    if (v == 1) {
+      *n1 = SplitV<P, 1>::N1;
+      *n2 = SplitV<P, 1>::N2;
+    }
+  }
+  if (v == 0) {
+    *n1 = SplitV<P, 0>::N1;
+    *n2 = SplitV<P, 0>::N2;
+  }
+}
+void split_of(int P, int v, int32_t* n1, int32_t* n2) {
+  *n1 = *n2 = 0;
+  CS_DISPATCH(P, split_into<PP>(v, n1, n2));
+}
+
+// the key of pass k at the handle's lengths in use
+TuneKey tune_key(const cs_ngf_fixed* f, int k) {
   const Geo& g = f->g;
-  { Stage sp(f, 1, st); CS_DISPATCH(g.Px, launch_fwd_x<PP>(f->Bh, f->Mh, f->F02, f->tw[2], g, nb, st)); }
-  if (cs_ngf_status s = check_launch("fwd_x")) return s;
-  { Stage sp(f, 2, st); CS_DISPATCH(g.Py, launch_fwd_y<PP>(f->F02, f->F13, f->tw[1], g, nb, st)); }
-  if (cs_ngf_status s = check_launch("fwd_y")) return s;
-  { Stage sp(f, 3, st); CS_DISPATCH(g.Pz, launch_zmac<PP>(f->F13, f->UV, f->F02, f->tw[0], g, nb, f->bounds, st)); }
-  if (cs_ngf_status s = check_launch("zmac")) return s;
-  { Stage sp(f, 4, st); CS_DISPATCH(g.Py, launch_inv_y<PP>(f->F02, f->F13, f->tw[1], g, nb, f->bounds, st)); }
-  if (cs_ngf_status s = check_launch("inv_y")) return s;
-  { Stage sp(f, 5, st); CS_DISPATCH(g.Px, launch_inv_x<PP>(f->F13, f->thr, f->keys, map, f->tw[2], g, nb, f->bounds, st)); }
-  if (cs_ngf_status s = check_launch("inv_x")) return s;
+  switch (k) {
+    case 0: return {0, g.Px, 2 * g.nx <= g.Px, g.store};
+    case 1: return {1, g.Py, 2 * g.ny <= g.Py, g.store};
+    case 2: return {2, g.Pz, 2 * g.nz <= g.Pz, g.store};
+    case 3: return {3, g.Py, 0, 0};
+    default: return {4, g.Px, 0, 0};
+  }
+}
+
+// the variants the handle uses at its lengths in use: the table's choices
+// when autotuning, else the built-in splits
+void resolve_variants(cs_ngf_fixed* f) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int k = 0; k < kPasses; ++k) {
+    f->vars[k] = 0;
+    if (!f->autotune) continue;
+    auto it = g_tune.find(tune_key(f, k));
+    if (it != g_tune.end()) f->vars[k] = it->second.variant;
+  }
+}
+
+// some pass at the lengths in use has two splits and no choice yet
+bool needs_tuning(const cs_ngf_fixed* f) {
+  if (!f->autotune) return false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int k = 0; k < kPasses; ++k) {
+    const TuneKey key = tune_key(f, k);
+    if (has_alt_split(key.P) && g_tune.find(key) == g_tune.end()) return true;
+  }
+  return false;
+}
+
+// launch FFT pass k of nb volumes with split variant v
+void launch_pass(cs_ngf_fixed* f, int k, int v, int nb, float* map, cudaStream_t st) {
+  const Geo& g = f->g;
+  switch (k) {
+    case 0: CS_DISPATCH(g.Px, launch_fwd_x<PP>(f->Bh, f->Mh, f->F02, f->tw[2], g, nb, st, v)); break;
+    case 1: CS_DISPATCH(g.Py, launch_fwd_y<PP>(f->F02, f->F13, f->tw[1], g, nb, st, v)); break;
+    case 2: CS_DISPATCH(g.Pz, launch_zmac<PP>(f->F13, f->UV, f->F02, f->tw[0], g, nb, f->bounds, st, v)); break;
+    case 3: CS_DISPATCH(g.Py, launch_inv_y<PP>(f->F02, f->F13, f->tw[1], g, nb, f->bounds, st, v)); break;
+    default: CS_DISPATCH(g.Px, launch_inv_x<PP>(f->F13, f->thr, f->keys, map, f->tw[2], g, nb, f->bounds, st, v)); break;
+  }
+}
+
+const char* const kPassName[kPasses] = {"fwd_x", "fwd_y", "zmac", "inv_y", "inv_x"};
+
+// Time both variants of pass k (best of two runs each, on the inputs the
+// previous passes left), record the faster and run it once more, so that
+// its output is what the next pass reads.  A pass is repeatable: it reads
+// buffers it does not write, except the x inverse's per-rotation maxima,
+// which are cleared before the final run.
+cs_ngf_status tune_pass(cs_ngf_fixed* f, int k, int nb, cudaStream_t st) {
+  const TuneKey key = tune_key(f, k);
+  float best[2] = {0.0f, 0.0f};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CS_CUDA(cudaEventCreate(&e0));
+  CS_CUDA(cudaEventCreate(&e1));
+  cs_ngf_status s = CS_NGF_OK;
+  for (int v = 0; v < 2 && !s; ++v)
+    for (int rep = 0; rep < 2 && !s; ++rep) {
+      cudaEventRecord(e0, st);
+      { Stage sp(f, 1 + k, st); launch_pass(f, k, v, nb, nullptr, st); }
+      cudaEventRecord(e1, st);
+      if ((s = check_launch(kPassName[k]))) break;
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        s = fail(CS_NGF_ECUDA, "autotune timing failed");
+      if (rep == 0 || ms < best[v]) best[v] = ms;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  const int choice = best[1] < best[0] ? 1 : 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {choice, {best[0], best[1]}};
+  }
+  f->vars[k] = choice;
+  if (k == 4) CS_CUDA(cudaMemsetAsync(f->keys, 0, sizeof(unsigned long long) * nb, st));
+  { Stage sp(f, 1 + k, st); launch_pass(f, k, choice, nb, nullptr, st); }
+  return check_launch(kPassName[k]);
+}
+
+// the FFT passes for nb volumes already resampled into f->Bh / f->Mh; with
+// tune, passes whose two splits have no choice yet are timed first
+cs_ngf_status run_transforms(cs_ngf_fixed* f, int nb, float* map, cudaStream_t st, bool tune = false) {
+  for (int k = 0; k < kPasses; ++k) {
+    if (tune && !map) {
+      const TuneKey key = tune_key(f, k);
+      bool untuned = false;
+      if (has_alt_split(key.P)) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        untuned = g_tune.find(key) == g_tune.end();
+      }
+      if (untuned) {
+        if (cs_ngf_status s = tune_pass(f, k, nb, st)) return s;
+        continue;
+      }
+    }
+    { Stage sp(f, 1 + k, st); launch_pass(f, k, f->vars[k], nb, map, st); }
+    if (cs_ngf_status s = check_launch(kPassName[k])) return s;
+  }
   return CS_NGF_OK;
 }
 
@@ -272,7 +403,7 @@ cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, 
 // score nb rotations whose matrices are at rot (device), with the floating
 // volume already packed in f->BM; results to out_score[nb], out_shift[nb][3]
 cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float* out_score,
-                               int32_t* out_shift, float* map, cudaStream_t st) {
+                               int32_t* out_shift, float* map, cudaStream_t st, bool tune = false) {
   const Geo& g = f->g;
   const size_t nmarg = (size_t)g.nz + g.ny + g.nx;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int) * nb, st));
@@ -299,7 +430,7 @@ cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float
     Stage sp(f, 7, st);
     k_fill<<<256, 256, 0, st>>>(map, (long long)g.vz * g.vy * g.vx, -INFINITY);
   }
-  if (cs_ngf_status s = run_transforms(f, nb, map, st)) return s;
+  if (cs_ngf_status s = run_transforms(f, nb, map, st, tune)) return s;
   {
     Stage sp(f, 7, st);
     k_finalize<<<(nb + 127) / 128, 128, 0, st>>>(f->keys, nb, g, out_score, out_shift);
@@ -310,14 +441,20 @@ cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float
 constexpr int kKernelsPerBatch = 9;   // resample, thresholds, bounds, 5 passes, finalize
 
 cs_ngf_status score_batch(cs_ngf_fixed* f, int r0, int nb, float* best_score, int32_t* best_shift,
-                          float* map, cudaStream_t st) {
-  return score_batch_ptrs(f, f->rot_d + r0, nb, best_score + r0, best_shift + 3 * (size_t)r0, map, st);
+                          float* map, cudaStream_t st, bool tune = false) {
+  return score_batch_ptrs(f, f->rot_d + r0, nb, best_score + r0, best_shift + 3 * (size_t)r0, map, st,
+                          tune);
 }
 
 // capture the full-batch launch sequence once (on a private stream; the
 // graph is then replayed on the caller's stream)
 cs_ngf_status ensure_graph(cs_ngf_fixed* f) {
+  if (f->gexec && !std::equal(f->vars, f->vars + kPasses, f->gexec_vars)) {   // captured with other splits
+    cudaGraphExecDestroy(f->gexec);
+    f->gexec = nullptr;
+  }
   if (f->gexec) return CS_NGF_OK;
+  std::copy(f->vars, f->vars + kPasses, f->gexec_vars);
   if (!f->rot_slot) {
     CS_CUDA(dalloc(&f->rot_slot, (size_t)f->batch));
     CS_CUDA(dalloc(&f->slot_score, (size_t)f->batch));
@@ -389,17 +526,23 @@ cs_ngf_status set_pads(cs_ngf_fixed* f, const int pad[3], cudaStream_t st) {
       if (cs_ngf_status s = fill_twiddles(pad[a], f->tw[a])) return s;
   // the captured launches hold the lengths: keep this graph for a later
   // return to them, and take the one of the new lengths if there is one
-  if (f->gexec) f->graphs.push_back({{g.Pz, g.Py, g.Px}, f->gexec});
+  if (f->gexec) {
+    cs_ngf_fixed::GraphSlot gs{{g.Pz, g.Py, g.Px}, {0, 0, 0, 0, 0}, f->gexec};
+    std::copy(f->gexec_vars, f->gexec_vars + kPasses, gs.vars);
+    f->graphs.push_back(gs);
+  }
   f->gexec = nullptr;
   for (size_t i = 0; i < f->graphs.size(); ++i)
     if (std::equal(pad, pad + 3, f->graphs[i].pad)) {
       f->gexec = f->graphs[i].exec;
+      std::copy(f->graphs[i].vars, f->graphs[i].vars + kPasses, f->gexec_vars);
       f->graphs.erase(f->graphs.begin() + (long)i);
       break;
     }
   g.Pz = pad[0];
   g.Py = pad[1];
   g.Px = pad[2];
+  resolve_variants(f);
   return run_fixed(f, f->A_keep, f->MA_keep, st);
 }
 
@@ -502,6 +645,10 @@ cs_ngf_status score_range_impl(cs_ngf_fixed* f, int r0_begin, int n, float* best
   const int end = r0_begin + n;
   for (int r0 = r0_begin; r0 < end; r0 += f->batch) {
     const int nb = std::min(f->batch, end - r0);
+    if (needs_tuning(f)) {                       // first group at these lengths: time the splits
+      if (cs_ngf_status s = score_batch(f, r0, nb, best_score, best_shift, nullptr, st, true)) return s;
+      continue;
+    }
     if (nb == f->batch && !f->profiling) {
       if (cs_ngf_status s = ensure_graph(f)) return s;
       CS_CUDA(cudaMemcpyAsync(f->rot_slot, f->rot_d + r0, sizeof(RotMat) * nb, cudaMemcpyDeviceToDevice, st));
@@ -665,6 +812,7 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
     return fail(CS_NGF_EINVAL, "unknown precision");
   if (cfg.pad_mode != CS_NGF_PAD_FULL && cfg.pad_mode != CS_NGF_PAD_BOUND)
     return fail(CS_NGF_EINVAL, "unknown pad_mode");
+  if (cfg.autotune != 0 && cfg.autotune != 1) return fail(CS_NGF_EINVAL, "autotune must be 0 or 1");
   for (int a = 0; a < 3; ++a) {
     pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
     if (!pad_supported(pad[a]))
@@ -810,6 +958,8 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   set_field_scales(g);
   for (int a = 0; a < 3; ++a) f->alloc_pad[a] = pad[a];
   f->pad_mode = cfg.pad_mode;
+  f->autotune = cfg.autotune != 0;
+  resolve_variants(f);
 
   const Sizes sz = sizes_for(dims, pad, cfg.measure, cfg.precision);
   f->f02_elems = sz.f02_elems;
@@ -982,6 +1132,32 @@ cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info) {
 }
 
 void cs_ngf_release(cs_ngf_fixed* f) { free_handle(f); }
+
+int32_t cs_ngf_tuning(int32_t cap, cs_ngf_tuning_entry* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int n = 0;
+  for (const auto& kv : g_tune) {
+    if (out && n < cap) {
+      cs_ngf_tuning_entry& e = out[n];
+      e.pass = kv.first.pass;
+      e.length = kv.first.P;
+      e.half_input = kv.first.half;
+      e.storage = kv.first.store;           // kStore* values equal the cs_ngf_precision codes
+      e.variant = kv.second.variant;
+      for (int v = 0; v < 2; ++v) {
+        e.ms[v] = kv.second.ms[v];
+        split_of(kv.first.P, v, &e.split[v][0], &e.split[v][1]);
+      }
+    }
+    ++n;
+  }
+  return n;
+}
+
+void cs_ngf_tuning_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
 
 int32_t cs_ngf_length_sets(const cs_ngf_fixed* f, int32_t cap, int32_t* pads, int32_t* counts) {
   if (!f) return 0;

@@ -213,26 +213,43 @@ struct Dft {
 };
 
 // ---------------------------------------------------------------- four-step
+// N = N1 * N2 with N1 <= N2 (step 2 then has at most one item per thread).
+// Split variant V = 0 is the built-in choice; V = 1, where a length has one,
+// is the alternative the autotuner times against it.
+template <int N, int V>
+struct SplitV;
+template <> struct SplitV<16, 0>  { static constexpr int N1 = 4,  N2 = 4; };
+template <> struct SplitV<32, 0>  { static constexpr int N1 = 4,  N2 = 8; };
+template <> struct SplitV<40, 0>  { static constexpr int N1 = 4,  N2 = 10; };
+template <> struct SplitV<64, 0>  { static constexpr int N1 = 8,  N2 = 8; };
+template <> struct SplitV<80, 0>  { static constexpr int N1 = 8,  N2 = 10; };
+template <> struct SplitV<100, 0> { static constexpr int N1 = 10, N2 = 10; };
+template <> struct SplitV<128, 0> { static constexpr int N1 = 8,  N2 = 16; };
+template <> struct SplitV<160, 0> { static constexpr int N1 = 8,  N2 = 20; };
+template <> struct SplitV<200, 0> { static constexpr int N1 = 10, N2 = 20; };
+template <> struct SplitV<256, 0> { static constexpr int N1 = 16, N2 = 16; };
+template <> struct SplitV<320, 0> { static constexpr int N1 = 16, N2 = 20; };
+template <> struct SplitV<400, 0> { static constexpr int N1 = 16, N2 = 25; };
+template <> struct SplitV<512, 0> { static constexpr int N1 = 16, N2 = 32; };
+template <> struct SplitV<64, 1>  { static constexpr int N1 = 4,  N2 = 16; };
+template <> struct SplitV<80, 1>  { static constexpr int N1 = 4,  N2 = 20; };
+template <> struct SplitV<128, 1> { static constexpr int N1 = 4,  N2 = 32; };
+template <> struct SplitV<160, 1> { static constexpr int N1 = 10, N2 = 16; };
+template <> struct SplitV<200, 1> { static constexpr int N1 = 8,  N2 = 25; };
+template <> struct SplitV<256, 1> { static constexpr int N1 = 8,  N2 = 32; };
+template <> struct SplitV<320, 1> { static constexpr int N1 = 10, N2 = 32; };
+template <> struct SplitV<400, 1> { static constexpr int N1 = 20, N2 = 20; };
+// lengths with a second split
+constexpr bool has_alt_split(int N) {
+  return N == 64 || N == 80 || N == 128 || N == 160 || N == 200 || N == 256 || N == 320 || N == 400;
+}
 template <int N>
-struct Split;   // N = N1 * N2 with N1 <= N2 (step 2 then has at most one item per thread)
-template <> struct Split<16>  { static constexpr int N1 = 4,  N2 = 4; };
-template <> struct Split<32>  { static constexpr int N1 = 4,  N2 = 8; };
-template <> struct Split<40>  { static constexpr int N1 = 4,  N2 = 10; };
-template <> struct Split<64>  { static constexpr int N1 = 8,  N2 = 8; };
-template <> struct Split<80>  { static constexpr int N1 = 8,  N2 = 10; };
-template <> struct Split<100> { static constexpr int N1 = 10, N2 = 10; };
-template <> struct Split<128> { static constexpr int N1 = 8,  N2 = 16; };
-template <> struct Split<160> { static constexpr int N1 = 8,  N2 = 20; };
-template <> struct Split<200> { static constexpr int N1 = 10, N2 = 20; };
-template <> struct Split<256> { static constexpr int N1 = 16, N2 = 16; };
-template <> struct Split<320> { static constexpr int N1 = 16, N2 = 20; };
-template <> struct Split<400> { static constexpr int N1 = 16, N2 = 25; };
-template <> struct Split<512> { static constexpr int N1 = 16, N2 = 32; };
+using Split = SplitV<N, 0>;
 
-template <int N, bool PAD_ROWS = true>
+template <int N, bool PAD_ROWS = true, int V = 0>
 struct FourStep {
-  static constexpr int N1 = Split<N>::N1;
-  static constexpr int N2 = Split<N>::N2;
+  static constexpr int N1 = SplitV<N, V>::N1;
+  static constexpr int N2 = SplitV<N, V>::N2;
   // exchange layout per sequence: [n2][k1] with padded strides (odd strides keep
   // 16 consecutive lanes on distinct bank pairs for either lane ordering).
   // Without row padding (RS = N1) a transformed sequence is in natural order;

@@ -36,8 +36,13 @@ struct cs_ngf_fixed {
   int length_sets = 1;         // sets of FFT lengths the last scoring call used
   std::vector<int> last_pads;  // their lengths [3 per set] and rotation counts
   std::vector<int> last_counts;
+  // split variant of each FFT pass at the lengths in use (fwd_x, fwd_y, zmac,
+  // inv_y, inv_x): 0 unless autotuning chose the alternative
+  bool autotune = false;
+  int vars[5] = {0, 0, 0, 0, 0};
+  int gexec_vars[5] = {0, 0, 0, 0, 0};   // the variants gexec was captured with
   // one captured graph per set of FFT lengths (all reference the same buffers)
-  struct GraphSlot { int pad[3]; cudaGraphExec_t exec; };
+  struct GraphSlot { int pad[3]; int vars[5]; cudaGraphExec_t exec; };
   std::vector<GraphSlot> graphs;
   size_t f02_elems = 0, f13_elems = 0;
   float2* UV = nullptr;

@@ -50,6 +50,12 @@ struct Geo {
 
 constexpr int kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2;
 
+// a[j] for a field index j known only at run time, without indexing the
+// kernel-parameter array (which would copy it to local memory)
+__device__ __forceinline__ float field_scale(const float (&a)[4], int j) {
+  return j == 0 ? a[0] : j == 1 ? a[1] : j == 2 ? a[2] : a[3];
+}
+
 // Storage of the packed fields of F0 / F1 for a batch of rotations: the
 // channel fields j < nch hold FP32 complex values, or 16-bit pairs in the
 // reduced-precision forms (BF16; FP16 with a per-field power-of-two scale);
@@ -155,20 +161,22 @@ __global__ void k_copy_in(const float* __restrict__ A, const uint8_t* __restrict
                           long long n, float* __restrict__ Bh, uint8_t* __restrict__ Mh);
 
 // ----------------------------------------------------------------- FFT passes
-// F0 / F1 are laid out by Fields<g.store> (FP32 everywhere when g.store == kStoreF32)
+// F0 / F1 are laid out by Fields<g.store> (FP32 everywhere when g.store == kStoreF32).
+// v: split variant of the length P (SplitV<P, v>; 0 = the built-in one, 1 =
+// the alternative where P has one, chosen by the autotuner)
 template <int P> void launch_fwd_x(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw,
-                                   Geo g, int nrot, cudaStream_t st);
+                                   Geo g, int nrot, cudaStream_t st, int v = 0);
 template <int P> void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int v = 0);
 template <int P> void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw,
-                                  Geo g, int nrot, const int* bounds, cudaStream_t st);
+                                  Geo g, int nrot, const int* bounds, cudaStream_t st, int v = 0);
 template <int P> void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g,
                                     cudaStream_t st);
 template <int P> void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nrot,
-                                   const int* bounds, cudaStream_t st);
+                                   const int* bounds, cudaStream_t st, int v = 0);
 template <int P> void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys,
                                    float* map, const float2* tw, Geo g, int nrot, const int* bounds,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int v = 0);
 // bounds: per rotation {lo_z, hi_z, lo_y, hi_y, lo_x, hi_x} shift slots that can
 // be valid, or nullptr for the full range
 

@@ -43,6 +43,18 @@ static void by_store(int store, F&& f) {
   else f(std::integral_constant<int, kStoreF32>{});
 }
 
+// calls f with split variant v of length P (0 where P has no second split)
+template <int P, class F>
+static void by_split(int v, F&& f) {
+  if constexpr (has_alt_split(P)) {
+    if (v == 1) {
+      f(std::integral_constant<int, 1>{});
+      return;
+    }
+  }
+  f(std::integral_constant<int, 0>{});
+}
+
 template <class K>
 static void set_smem(K kern, size_t bytes) {
   if (bytes > 48 * 1024)
@@ -57,20 +69,21 @@ static void set_smem(K kern, size_t bytes) {
 // A thread keeps the NGF (x, y, z, mask) of its step-1 inputs across the
 // four fields: in registers for half-length inputs, in its own slots of
 // shared memory [NI][NT] (float4) for full-length ones, which would spill.
-template <int P, bool HALF>
+template <int P, bool HALF, int V>
 struct FwdXCfg {
-  static constexpr int ROWS = (256 / Split<P>::N2) > 0 ? (256 / Split<P>::N2) : 1;
-  static constexpr int NT = ROWS * Split<P>::N2;
-  static constexpr int NI = FwdIn<FourStep<P>, HALF>::NI;
-  static constexpr size_t ex_bytes = ((size_t)ROWS * FourStep<P>::CS * sizeof(float2) + 15) / 16 * 16;
+  static constexpr int N2 = SplitV<P, V>::N2;
+  static constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
+  static constexpr int NT = ROWS * N2;
+  static constexpr int NI = FwdIn<FourStep<P, true, V>, HALF>::NI;
+  static constexpr size_t ex_bytes = ((size_t)ROWS * FourStep<P, true, V>::CS * sizeof(float2) + 15) / 16 * 16;
   static constexpr size_t smem_bytes = ex_bytes + (HALF ? 0 : (size_t)NI * NT * sizeof(float4));
 };
 
-template <int P, int ROWS, int ST, bool HALF>
-__global__ void __launch_bounds__(ROWS * Split<P>::N2, 2)
+template <int P, int ROWS, int ST, bool HALF, int V>
+__global__ void __launch_bounds__(ROWS * SplitV<P, V>::N2, 2)
 k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __restrict__ F0,
         const float2* __restrict__ tw, Geo g, long long nrows) {
-  using FS = FourStep<P>;
+  using FS = FourStep<P, true, V>;
   using FI = FwdIn<FS, HALF>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, H = FI::NI;
   extern __shared__ float2 ex[];
@@ -86,9 +99,9 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
   constexpr bool NS = !HALF;                  // NGF staged in shared memory
   constexpr int HR = NS ? 1 : H;
   float vx[HR], vy[HR], vz[HR], mm[HR];
-  float4* ngs = reinterpret_cast<float4*>(reinterpret_cast<char*>(ex) + FwdXCfg<P, HALF>::ex_bytes);
+  float4* ngs = reinterpret_cast<float4*>(reinterpret_cast<char*>(ex) + FwdXCfg<P, HALF, V>::ex_bytes);
   const int NTX = ROWS * N2;
-  const float* V = Bh + (long long)r * g.nvox;
+  const float* Vol = Bh + (long long)r * g.nvox;
   const uint8_t* M = Mh + (long long)r * g.nvox;
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   const int ym = max(y - 1, 0), yp = min(y + 1, g.ny - 1);
@@ -100,11 +113,11 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
     float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (row_ok && x < g.nx) {
       const int xm = max(x - 1, 0), xp = min(x + 1, g.nx - 1);
-      const float gx = 0.5f * (__ldg(&V[base + xp]) - __ldg(&V[base + xm]));
-      const float gy = 0.5f * (__ldg(&V[(long long)z * sz + (long long)yp * sy + x]) -
-                               __ldg(&V[(long long)z * sz + (long long)ym * sy + x]));
-      const float gz = 0.5f * (__ldg(&V[(long long)zp * sz + (long long)y * sy + x]) -
-                               __ldg(&V[(long long)zm * sz + (long long)y * sy + x]));
+      const float gx = 0.5f * (__ldg(&Vol[base + xp]) - __ldg(&Vol[base + xm]));
+      const float gy = 0.5f * (__ldg(&Vol[(long long)z * sz + (long long)yp * sy + x]) -
+                               __ldg(&Vol[(long long)z * sz + (long long)ym * sy + x]));
+      const float gz = 0.5f * (__ldg(&Vol[(long long)zp * sz + (long long)y * sy + x]) -
+                               __ldg(&Vol[(long long)zm * sz + (long long)y * sy + x]));
       const float inv = rsqrtf(gx * gx + gy * gy + gz * gz + g.eps2);
       q = make_float4(gx * inv, gy * inv, gz * inv, M[base + x] ? 1.0f : 0.0f);
     }
@@ -171,7 +184,7 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
         const int r2 = (int)(rz2 / g.nz), z2 = (int)(rz2 - (long long)r2 * g.nz);
         char* fld = Fields<ST>::field(F0, g, rows_per_field * P, r2, j);
         const long long row = ((long long)z2 * g.ny + y2) * P;
-        const float sc = g.scale0[j];
+        const float sc = field_scale(g.scale0, j);
         if (j == g.nch) {
 #pragma unroll
           for (int k2 = 0; k2 < N2; ++k2) Fields<ST>::put(fld, row + k1 + N1 * k2, u[k2], true, sc);
@@ -185,26 +198,29 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
   }
 }
 
-template <int P, bool HALF>
+template <int P, bool HALF, int V>
 void launch_fwd_x_t(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw, Geo g, int nrot,
                     cudaStream_t st) {
-  constexpr int N2 = Split<P>::N2;
-  constexpr int ROWS = FwdXCfg<P, HALF>::ROWS;
+  constexpr int N2 = SplitV<P, V>::N2;
+  constexpr int ROWS = FwdXCfg<P, HALF, V>::ROWS;
   const long long nrows = (long long)nrot * g.nz * g.ny;
-  const size_t smem = FwdXCfg<P, HALF>::smem_bytes;
+  const size_t smem = FwdXCfg<P, HALF, V>::smem_bytes;
   const unsigned blocks = (unsigned)((nrows + ROWS - 1) / ROWS);
   auto go = [&](auto kern) {
     set_smem(kern, smem);
     kern<<<blocks, ROWS * N2, smem, st>>>(Bh, Mh, F0, tw, g, nrows);
   };
-  by_store(g.store, [&](auto st) { go(k_fwd_x<P, ROWS, decltype(st)::value, HALF>); });
+  by_store(g.store, [&](auto st) { go(k_fwd_x<P, ROWS, decltype(st)::value, HALF, V>); });
 }
 
 template <int P>
 void launch_fwd_x(const float* Bh, const uint8_t* Mh, void* F0, const float2* tw, Geo g, int nrot,
-                  cudaStream_t st) {
-  if (2 * g.nx <= P) launch_fwd_x_t<P, true>(Bh, Mh, F0, tw, g, nrot, st);
-  else launch_fwd_x_t<P, false>(Bh, Mh, F0, tw, g, nrot, st);
+                  cudaStream_t st, int v) {
+  by_split<P>(v, [&](auto vc) {
+    constexpr int V = decltype(vc)::value;
+    if (2 * g.nx <= P) launch_fwd_x_t<P, true, V>(Bh, Mh, F0, tw, g, nrot, st);
+    else launch_fwd_x_t<P, false, V>(Bh, Mh, F0, tw, g, nrot, st);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -224,21 +240,21 @@ constexpr int pass_blocks(int threads, size_t smem, int minr) {
   }
   return best;
 }
-template <int P> struct FwdYCfg {
+template <int P, int V> struct FwdYCfg {
   // 16 columns per block; 8 where the second stage is longer than 20 points
   // (more registers per thread: smaller blocks keep several per SM)
-  static constexpr int W = Split<P>::N2 > 20 ? 8 : 16;
-  static constexpr int NT = W * Split<P>::N2;
-  static constexpr size_t smem_bytes = (size_t)W * FourStep<P>::CS * sizeof(float2);
+  static constexpr int W = SplitV<P, V>::N2 > 20 ? 8 : 16;
+  static constexpr int NT = W * SplitV<P, V>::N2;
+  static constexpr size_t smem_bytes = (size_t)W * FourStep<P, true, V>::CS * sizeof(float2);
   // the 25- and 32-point second stages need more registers than 16- or 20-point ones
-  static constexpr int MIN_BLOCKS = pass_blocks(NT, smem_bytes, Split<P>::N2 > 20 ? 80 : 48);
+  static constexpr int MIN_BLOCKS = pass_blocks(NT, smem_bytes, SplitV<P, V>::N2 > 20 ? 80 : 48);
 };
 
-template <int P, int W, int ST, bool HALF>
-__global__ void __launch_bounds__(W * Split<P>::N2, FwdYCfg<P>::MIN_BLOCKS)
+template <int P, int W, int ST, bool HALF, int V>
+__global__ void __launch_bounds__(W * SplitV<P, V>::N2, FwdYCfg<P, V>::MIN_BLOCKS)
 k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __restrict__ tw,
         Geo g) {
-  using FS = FourStep<P>;
+  using FS = FourStep<P, true, V>;
   using FI = FwdIn<FS, HALF>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
   extern __shared__ float2 ex[];
@@ -256,7 +272,7 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
     const int col = t % W, n2 = t / W;
     const int kx = kx0 + col;
     const char* src = Fields<ST>::field(F0, g, (long long)g.nz * g.ny * g.Px, r, j);
-    const float isc = 1.0f / g.scale0[j];
+    const float isc = 1.0f / field_scale(g.scale0, j);
     const long long zoff = (long long)z * g.ny * g.Px;
     float2 v[FI::NI];                     // y < ny: with ny <= P/2 the upper half is zero
     if (is_mask) {
@@ -285,7 +301,7 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
       FS::template step2<-1>(u, ex + col * CS, k1);
       char* dst = Fields<ST>::field(F1, g, (long long)g.nz * g.Px * P, r, j);
       const long long row = ((long long)kx * g.nz + z) * P;       // [kx][z][ky]
-      const float sc = g.scale1[j];
+      const float sc = field_scale(g.scale1, j);
       if (is_mask) {
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) Fields<ST>::put(dst, row + k1 + N1 * k2, u[k2], true, sc);
@@ -297,20 +313,25 @@ k_fwd_y(const void* __restrict__ F0, void* __restrict__ F1, const float2* __rest
   }
 }
 
-template <int P>
-void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, cudaStream_t st) {
-  constexpr int W = FwdYCfg<P>::W, N2 = Split<P>::N2;
-  const size_t smem = FwdYCfg<P>::smem_bytes;
+template <int P, int V>
+void launch_fwd_y_t(const void* F0, void* F1, const float2* tw, Geo g, int nrot, cudaStream_t st) {
+  constexpr int W = FwdYCfg<P, V>::W, N2 = SplitV<P, V>::N2;
+  const size_t smem = FwdYCfg<P, V>::smem_bytes;
   dim3 grid((unsigned)((g.Px + W - 1) / W), (unsigned)(nrot * g.nf * g.nz));   // y: at most 32 * 4 * 256
   auto go = [&](auto kern) {
     set_smem(kern, smem);
     kern<<<grid, W * N2, smem, st>>>(F0, F1, tw, g);
   };
   const bool half = 2 * g.ny <= P;
-  by_store(g.store, [&](auto st) {
-    constexpr int ST = decltype(st)::value;
-    half ? go(k_fwd_y<P, W, ST, true>) : go(k_fwd_y<P, W, ST, false>);
+  by_store(g.store, [&](auto sf) {
+    constexpr int ST = decltype(sf)::value;
+    half ? go(k_fwd_y<P, W, ST, true, V>) : go(k_fwd_y<P, W, ST, false, V>);
   });
+}
+
+template <int P>
+void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, cudaStream_t st, int v) {
+  by_split<P>(v, [&](auto vc) { launch_fwd_y_t<P, decltype(vc)::value>(F0, F1, tw, g, nrot, st); });
 }
 
 // ---------------------------------------------------------------------------
@@ -323,31 +344,31 @@ void launch_fwd_y(const void* F0, void* F1, const float2* tw, Geo g, int nrot, c
 // fixed spectra tile stays in L2.
 // ---------------------------------------------------------------------------
 // shared memory of a zmac block with W primary columns (see ZmacCfg)
-template <int P, bool HALF>
+template <int P, bool HALF, int V>
 constexpr size_t zmac_smem_base(int W) {
-  const int NI = HALF ? Split<P>::N1 / 2 : Split<P>::N1;
-  const size_t cs = 2 * W < 16 ? FourStep<P, true>::CS : FourStep<P, false>::CS;
-  return ((size_t)7 * W * P + (size_t)2 * W * cs + (size_t)2 * NI * (2 * W * Split<P>::N2)) *
+  const int NI = HALF ? SplitV<P, V>::N1 / 2 : SplitV<P, V>::N1;
+  const size_t cs = 2 * W < 16 ? FourStep<P, true, V>::CS : FourStep<P, false, V>::CS;
+  return ((size_t)7 * W * P + (size_t)2 * W * cs + (size_t)2 * NI * (2 * W * SplitV<P, V>::N2)) *
          sizeof(float2);
 }
 
-template <int P, bool HALF>
+template <int P, bool HALF, int V>
 struct ZmacCfg {
   // primary columns per block: the block's tile of the seven fixed spectra
   // (7 * W * P complex values) stays in shared memory for the whole batch;
   // 8 columns where the tile, the exchange and two input stages fit (at most
   // 227 KB per block), else 4
   static constexpr int W =
-      (P <= 320 && zmac_smem_base<P, HALF>(8) + P * sizeof(float2) <= 232448) ? 8 : 4;
-  static constexpr int NT = 2 * W * Split<P>::N2;
+      (P <= 320 && zmac_smem_base<P, HALF, V>(8) + P * sizeof(float2) <= 232448) ? 8 : 4;
+  static constexpr int NT = 2 * W * SplitV<P, V>::N2;
   // exchange rows unpadded when 16 columns fill a half-warp (natural order)
   static constexpr bool PAD = 2 * W < 16;
-  using FS = FourStep<P, PAD>;
+  using FS = FourStep<P, PAD, V>;
   static constexpr int NI = FwdIn<FS, HALF>::NI;   // staged inputs per thread and field
   // shared memory: fixed-spectra tile [7][W][P], transform exchange [2W][CS],
   // two stages of field inputs [2][NI][NT] and, where it does not cost a
   // second block per SM, the twiddle table [P] (else twiddles come from L1)
-  static constexpr size_t smem_base = zmac_smem_base<P, HALF>(W);
+  static constexpr size_t smem_base = zmac_smem_base<P, HALF, V>(W);
   static constexpr bool fits2(size_t b) { return 2 * (b + 1024) <= 228 * 1024; }   // per-block reserve
   static constexpr bool TWS = fits2(smem_base + P * sizeof(float2)) || !fits2(smem_base);
   static constexpr size_t smem_bytes = smem_base + (TWS ? P * sizeof(float2) : 0);
@@ -362,11 +383,11 @@ struct ZmacCfg {
   static constexpr int MIN_BLOCKS = (fits2(smem_bytes) && regs_for(2) >= 128) ? 2 : 1;
 };
 
-template <int P, int ST, bool HALF>
-__global__ void __launch_bounds__(ZmacCfg<P, HALF>::NT, ZmacCfg<P, HALF>::MIN_BLOCKS)
+template <int P, int ST, bool HALF, int V>
+__global__ void __launch_bounds__(ZmacCfg<P, HALF, V>::NT, ZmacCfg<P, HALF, V>::MIN_BLOCKS)
 k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __restrict__ F2,
        const float2* __restrict__ tw, Geo g, int nrot, const int* __restrict__ bounds) {
-  using C = ZmacCfg<P, HALF>;
+  using C = ZmacCfg<P, HALF, V>;
   using FS = typename C::FS;
   using FI = FwdIn<FS, HALF>;
   constexpr int W = C::W;
@@ -446,7 +467,7 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
       for (int n1 = 0; n1 < H; ++n1)
         v[n1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(buf + n1 * NT + t));
     } else {                                   // FP16: undo the field's power-of-two scale
-      const float isc = 1.0f / g.scale1[j];
+      const float isc = 1.0f / field_scale(g.scale1, j);
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) {
         const float2 h = __half22float2(*reinterpret_cast<const __half2*>(buf + n1 * NT + t));
@@ -580,23 +601,26 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   }
 }
 
-template <int P, bool HALF>
+template <int P, bool HALF, int V>
 void launch_zmac_t(const void* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
                    const int* bounds, cudaStream_t st) {
-  using C = ZmacCfg<P, HALF>;
+  using C = ZmacCfg<P, HALF, V>;
   dim3 grid((unsigned)((g.Py + C::W - 1) / C::W), (unsigned)(g.Px / 2 + 1));
   by_store(g.store, [&](auto sf) {
     constexpr int ST = decltype(sf)::value;
-    set_smem(k_zmac<P, ST, HALF>, C::smem_bytes);
-    k_zmac<P, ST, HALF><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
+    set_smem(k_zmac<P, ST, HALF, V>, C::smem_bytes);
+    k_zmac<P, ST, HALF, V><<<grid, C::NT, C::smem_bytes, st>>>(F1, UV, F2, tw, g, nrot, bounds);
   });
 }
 
 template <int P>
 void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
-                 const int* bounds, cudaStream_t st) {
-  if (2 * g.nz <= P) launch_zmac_t<P, true>(F1, UV, F2, tw, g, nrot, bounds, st);
-  else launch_zmac_t<P, false>(F1, UV, F2, tw, g, nrot, bounds, st);
+                 const int* bounds, cudaStream_t st, int v) {
+  by_split<P>(v, [&](auto vc) {
+    constexpr int V = decltype(vc)::value;
+    if (2 * g.nz <= P) launch_zmac_t<P, true, V>(F1, UV, F2, tw, g, nrot, bounds, st);
+    else launch_zmac_t<P, false, V>(F1, UV, F2, tw, g, nrot, bounds, st);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -699,11 +723,11 @@ void launch_prep_z(const float2* F1, float2* UV, const float2* tw, Geo g, cudaSt
 // inv_y: y-axis inverse FFT of every (vz, kx) row of F2, keeping 2ny-1 shift
 // rows, transposed so kx is contiguous.  Block: W consecutive kx rows.
 // ---------------------------------------------------------------------------
-template <int P, int W>
-__global__ void __launch_bounds__(W * Split<P>::N2)
+template <int P, int W, int V>
+__global__ void __launch_bounds__(W * SplitV<P, V>::N2)
 k_inv_y(const float2* __restrict__ F2, float2* __restrict__ F3, const float2* __restrict__ tw,
         Geo g, const int* __restrict__ bounds) {
-  using FS = FourStep<P>;
+  using FS = FourStep<P, true, V>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS;
   extern __shared__ float2 ex[];
   const int t = threadIdx.x;
@@ -745,12 +769,15 @@ k_inv_y(const float2* __restrict__ F2, float2* __restrict__ F3, const float2* __
 
 template <int P>
 void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nrot, const int* bounds,
-                  cudaStream_t st) {
-  constexpr int W = 16, N2 = Split<P>::N2;
-  const size_t smem = (size_t)W * FourStep<P>::CS * sizeof(float2);
-  set_smem(k_inv_y<P, W>, smem);
-  dim3 grid((unsigned)(nrot * g.vz), (unsigned)((g.Px + W - 1) / W));
-  k_inv_y<P, W><<<grid, W * N2, smem, st>>>(F2, F3, tw, g, bounds);
+                  cudaStream_t st, int v) {
+  by_split<P>(v, [&](auto vc) {
+    constexpr int V = decltype(vc)::value;
+    constexpr int W = 16, N2 = SplitV<P, V>::N2;
+    const size_t smem = (size_t)W * FourStep<P, true, V>::CS * sizeof(float2);
+    set_smem(k_inv_y<P, W, V>, smem);
+    dim3 grid((unsigned)(nrot * g.vz), (unsigned)((g.Px + W - 1) / W));
+    k_inv_y<P, W, V><<<grid, W * N2, smem, st>>>(F2, F3, tw, g, bounds);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -759,12 +786,12 @@ void launch_inv_y(const float2* F2, float2* F3, const float2* tw, Geo g, int nro
 // folded into the rotation's key with one atomicMax.  Optionally writes the
 // score map (-inf where invalid).  Block: ROWS consecutive vy of one plane.
 // ---------------------------------------------------------------------------
-template <int P, int ROWS>
-__global__ void __launch_bounds__((ROWS * Split<P>::N2 + 31) / 32 * 32)
+template <int P, int ROWS, int V>
+__global__ void __launch_bounds__((ROWS * SplitV<P, V>::N2 + 31) / 32 * 32)
 k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
         unsigned long long* __restrict__ keys, float* __restrict__ map,
         const float2* __restrict__ tw, Geo g, const int* __restrict__ bounds) {
-  using FS = FourStep<P>;
+  using FS = FourStep<P, true, V>;
   constexpr int N1 = FS::N1, N2 = FS::N2, CS = FS::CS, NT = (ROWS * N2 + 31) / 32 * 32;
   extern __shared__ float2 ex[];
   __shared__ unsigned long long red[NT / 32];
@@ -831,25 +858,28 @@ k_inv_x(const float2* __restrict__ F3, const float* __restrict__ thr,
 
 template <int P>
 void launch_inv_x(const float2* F3, const float* thr, unsigned long long* keys, float* map,
-                  const float2* tw, Geo g, int nrot, const int* bounds, cudaStream_t st) {
-  constexpr int N2 = Split<P>::N2;
-  constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
-  const size_t smem = (size_t)ROWS * FourStep<P>::CS * sizeof(float2);
-  set_smem(k_inv_x<P, ROWS>, smem);
-  dim3 grid((unsigned)((g.vy + ROWS - 1) / ROWS), (unsigned)(nrot * g.vz));
-  k_inv_x<P, ROWS><<<grid, (ROWS * N2 + 31) / 32 * 32, smem, st>>>(F3, thr, keys, map, tw, g, bounds);
+                  const float2* tw, Geo g, int nrot, const int* bounds, cudaStream_t st, int v) {
+  by_split<P>(v, [&](auto vc) {
+    constexpr int V = decltype(vc)::value;
+    constexpr int N2 = SplitV<P, V>::N2;
+    constexpr int ROWS = (256 / N2) > 0 ? (256 / N2) : 1;
+    const size_t smem = (size_t)ROWS * FourStep<P, true, V>::CS * sizeof(float2);
+    set_smem(k_inv_x<P, ROWS, V>, smem);
+    dim3 grid((unsigned)((g.vy + ROWS - 1) / ROWS), (unsigned)(nrot * g.vz));
+    k_inv_x<P, ROWS, V><<<grid, (ROWS * N2 + 31) / 32 * 32, smem, st>>>(F3, thr, keys, map, tw, g, bounds);
+  });
 }
 
 #define CSNGF_INSTANTIATE_PASSES(P)                                                              \
   template void launch_fwd_x<P>(const float*, const uint8_t*, void*, const float2*, Geo, int,    \
-                                cudaStream_t);                                                   \
-  template void launch_fwd_y<P>(const void*, void*, const float2*, Geo, int, cudaStream_t);      \
+                                cudaStream_t, int);                                              \
+  template void launch_fwd_y<P>(const void*, void*, const float2*, Geo, int, cudaStream_t, int); \
   template void launch_zmac<P>(const void*, const float2*, float2*, const float2*, Geo, int,      \
-                               const int*, cudaStream_t);                                        \
+                               const int*, cudaStream_t, int);                                   \
   template void launch_prep_z<P>(const float2*, float2*, const float2*, Geo, cudaStream_t);      \
   template void launch_inv_y<P>(const float2*, float2*, const float2*, Geo, int, const int*,     \
-                                cudaStream_t);                                                   \
+                                cudaStream_t, int);                                              \
   template void launch_inv_x<P>(const float2*, const float*, unsigned long long*, float*,        \
-                                const float2*, Geo, int, const int*, cudaStream_t);
+                                const float2*, Geo, int, const int*, cudaStream_t, int);
 
 }  // namespace csngf

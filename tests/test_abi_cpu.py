@@ -67,11 +67,17 @@ def test_prepare_rejects_bad_arguments_before_touching_the_device(binding):
     lib.cs_ngf_default_config(ctypes.byref(cfg))
     assert cfg.eps == pytest.approx(1e-5) and cfg.gamma == 0.5
     assert cfg.pad_mode == binding.PAD_MODES["bound"]      # bound-limited padding by default
-    assert ctypes.sizeof(binding.Config) == 36 and ctypes.sizeof(binding.Info) == 80
+    assert ctypes.sizeof(binding.Config) == 40 and ctypes.sizeof(binding.Info) == 80
     cfg.pad_mode = 5
     assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None, ctypes.byref(h)) == binding.EINVAL
     assert b"pad_mode" in lib.cs_ngf_last_error()
     cfg.pad_mode = binding.PAD_MODES["full"]
+    assert cfg.autotune == 0
+    cfg.autotune = 2
+    assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None, ctypes.byref(h)) == binding.EINVAL
+    assert b"autotune" in lib.cs_ngf_last_error()
+    cfg.autotune = 1
+    assert binding.tuning() == []           # nothing timed in this process
     cfg.gamma = 1.5
     assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None, ctypes.byref(h)) == binding.EINVAL
     cfg.gamma = 0.5
