@@ -371,7 +371,14 @@ struct ZmacCfg {
   static constexpr size_t smem_base = zmac_smem_base<P, HALF, V>(W);
   static constexpr bool fits2(size_t b) { return 2 * (b + 1024) <= 228 * 1024; }   // per-block reserve
   static constexpr bool TWS = fits2(smem_base + P * sizeof(float2)) || !fits2(smem_base);
-  static constexpr size_t smem_bytes = smem_base + (TWS ? P * sizeof(float2) : 0);
+  static constexpr size_t smem_one = smem_base + (TWS ? P * sizeof(float2) : 0);
+  // a second exchange buffer, used by alternate fields, where it fits without
+  // costing a block per SM: the next field's first step then need not wait
+  // for this field's multiply-accumulate to finish reading
+  static constexpr size_t ex_bytes = (size_t)2 * W * FS::CS * sizeof(float2);
+  static constexpr int EXB =
+      (smem_one + ex_bytes <= 232448 && fits2(smem_one + ex_bytes) == fits2(smem_one)) ? 2 : 1;
+  static constexpr size_t smem_bytes = smem_one + (EXB - 1) * ex_bytes;
   // Registers per thread when B blocks share an SM: each of the SM's four
   // sub-partitions holds 16384 registers and the warps placed on it, at most
   // ceil(B * warps / 4) of them (allocation in multiples of 8 per thread).
@@ -396,8 +403,9 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   constexpr int TILE = W * P;                 // complex values per fixed-spectra tile
   extern __shared__ __align__(16) float2 smem[];
   float2* uvs = smem;                         // [7][W][P] fixed-spectra weights
-  float2* ex = smem + 7 * TILE;               // [NC][CS] transform exchange
-  float2* stage = ex + NC * CS;               // [2][H][NT] inputs of the next two fields
+  constexpr int EXB = C::EXB;
+  float2* ex0 = smem + 7 * TILE;              // [EXB][NC][CS] transform exchange
+  float2* stage = ex0 + EXB * NC * CS;        // [2][H][NT] inputs of the next two fields
                                               // (each thread uses only its own slots)
   float2* tws = stage + 2 * H * NT;           // [P] twiddles
   // a transformed column stays in the exchange slots of the four-step split:
@@ -458,7 +466,6 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
   // this thread's staged inputs of field j from buf, once all but the most
   // recent copy group have landed
   auto take = [&](float2 (&v)[H], const float2* buf, int j) {
-    cp_async_wait_one();
     if (ST == kStoreF32 || j == g.nch) {
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) v[n1] = buf[n1 * NT + t];
@@ -510,26 +517,10 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
       X[m] = make_float2(0.f, 0.f);
       Y[m] = (r & 1) ? Yn[m] : make_float2(0.f, 0.f);
     }
-#pragma unroll 1
-    for (int j = 0; j < nfr(r); ++j, ++f) {
-      float2* buf = stage + (f & 1) * H * NT;
-      float2 v[H];
-      take(v, buf, j);
-      FI::template step1<-1, TWS>(v, ex + c1 * CS, n2, twz);
-      __syncthreads();                         // (also orders this thread's reads of buf
-                                               //  before the next copies into it)
-      fetch(buf);                              // two fields ahead
-      if (has2) {
-        // in place: the outputs X[k1 + N1*k2] go to the slots k2*RS + k1 this
-        // thread has just read, so no other thread's reads are overtaken
-        float2 u[N2];
-        FS::template step2<-1>(u, ex + c2 * CS, k1);
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) ex[c2 * CS + k2 * FS::RS + k1] = u[k2];
-      }
-      __syncthreads();
-      // Eq. 7-8: the weighted channel products (separated through the mirror
-      // column) and the mask product, accumulated in registers
+    // Eq. 7-8: the weighted channel products (separated through the mirror
+    // column) and the mask product of field j, transformed in exb,
+    // accumulated in registers
+    auto mac = [&](int j, const float2* exb) {
       if (j < g.nch) {
         const float2* Us = uvs + (2 * j) * TILE;
         const float2* Vs = uvs + (2 * j + 1) * TILE;
@@ -538,8 +529,8 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
           const int i = t + NT * m;
           if (i < TILE) {
             const int c = i / P, kz = i - c * P;
-            const float2 h = ex[c * CS + slot(kz)];
-            const float2 hm = cconj(ex[(W + c) * CS + slot(kz == 0 ? 0 : P - kz)]);
+            const float2 h = exb[c * CS + slot(kz)];
+            const float2 hm = cconj(exb[(W + c) * CS + slot(kz == 0 ? 0 : P - kz)]);
             X[m] = cadd(X[m], cadd(cmul(Us[i], h), cmul(Vs[i], hm)));
           }
         }
@@ -551,8 +542,8 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
           const int i = t + NT * m;
           if (i < TILE) {
             const int c = i / P, kz = i - c * P;
-            const float2 h = ex[c * CS + slot(kz)];
-            const float2 hm = cconj(ex[(W + c) * CS + slot(kz == 0 ? 0 : P - kz)]);
+            const float2 h = exb[c * CS + slot(kz)];
+            const float2 hm = cconj(exb[(W + c) * CS + slot(kz == 0 ? 0 : P - kz)]);
             const float2 U = Ms[i];
             Y[m] = cmul(U, cscale(cadd(h, hm), 0.5f));
             const float2 d = cscale(csub(h, hm), 0.5f);
@@ -560,8 +551,63 @@ k_zmac(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __res
           }
         }
       }
-      __syncthreads();
+    };
+    // step 2 of one column sequence (column cc, k1), in place: the outputs
+    // X[k1 + N1*k2] go to the slots k2*RS + k1 this thread has just read, so
+    // no other thread's reads are overtaken
+    auto step2_at = [&](float2* exb, int cc, int kk) {
+      float2 u[N2];
+      FS::template step2<-1>(u, exb + cc * CS, kk);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) exb[cc * CS + k2 * FS::RS + kk] = u[k2];
+    };
+#pragma unroll 1
+    for (int j = 0; j < nfr(r);) {
+      if (EXB == 2 && j + 1 < nfr(r)) {
+        // two fields at once, in the two exchanges: both first steps, one
+        // barrier, both second steps spread over all threads, one barrier,
+        // both products, one barrier
+        float2* ex1 = ex0 + NC * CS;
+        cp_async_wait_all();                   // both fields' inputs have landed
+        {
+          float2 v[H];
+          take(v, stage + (f & 1) * H * NT, j);
+          FI::template step1<-1, TWS>(v, ex0 + c1 * CS, n2, twz);
+          take(v, stage + ((f + 1) & 1) * H * NT, j + 1);
+          FI::template step1<-1, TWS>(v, ex1 + c1 * CS, n2, twz);
+        }
+        __syncthreads();                       // (also orders this thread's reads of the
+                                               //  stages before the next copies into them)
+        fetch(stage + (f & 1) * H * NT);       // the next two fields
+        fetch(stage + ((f + 1) & 1) * H * NT);
+        for (int w = t; w < 2 * NC * N1; w += NT) {
+          const int q = w < NC * N1 ? w : w - NC * N1;
+          step2_at(w < NC * N1 ? ex0 : ex1, q % NC, q / NC);
+        }
+        __syncthreads();
+        mac(j, ex0);
+        mac(j + 1, ex1);
+        __syncthreads();
+        j += 2;
+        f += 2;
+      } else {
+        float2* buf = stage + (f & 1) * H * NT;
+        cp_async_wait_one();                   // all but the most recent copy group
+        float2 v[H];
+        take(v, buf, j);
+        FI::template step1<-1, TWS>(v, ex0 + c1 * CS, n2, twz);
+        __syncthreads();                       // (also orders this thread's reads of buf
+                                               //  before the next copies into it)
+        fetch(buf);                            // two fields ahead
+        if (has2) step2_at(ex0, c2, k1);
+        __syncthreads();
+        mac(j, ex0);
+        __syncthreads();
+        ++j;
+        ++f;
+      }
     }
+    float2* ex = ex0;                         // the rotation's inverse
     // Z = X + iY at k, conj(X) + i conj(Y) at -k
 #pragma unroll
     for (int m = 0; m < MI; ++m) {
