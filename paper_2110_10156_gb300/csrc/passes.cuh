@@ -107,6 +107,12 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
   const int ym = max(y - 1, 0), yp = min(y + 1, g.ny - 1);
   const int zm = max(z - 1, 0), zp = min(z + 1, g.nz - 1);
   const long long base = (long long)z * sz + (long long)y * sy;
+  const long long rows_per_field = (long long)g.nz * g.ny;
+  const int nrot = (int)(nrows / rows_per_field);
+  const bool has_partner = !(r & 1) && r + 1 < nrot;
+  // per element: the NGF times the mask (m^2 = m, so every Eq. 6 product of
+  // two masked components equals the product times m, bit for bit) and the
+  // mask pair of the mask field coded as m + 2 m2 (m2: the next rotation's mask)
 #pragma unroll
   for (int n1 = 0; n1 < H; ++n1) {
     const int x = N2 * n1 + n2;
@@ -119,7 +125,9 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
       const float gz = 0.5f * (__ldg(&Vol[(long long)zp * sz + (long long)y * sy + x]) -
                                __ldg(&Vol[(long long)zm * sz + (long long)y * sy + x]));
       const float inv = rsqrtf(gx * gx + gy * gy + gz * gz + g.eps2);
-      q = make_float4(gx * inv, gy * inv, gz * inv, M[base + x] ? 1.0f : 0.0f);
+      const float m = M[base + x] ? 1.0f : 0.0f;
+      const float m2 = (has_partner && M[g.nvox + base + x]) ? 2.0f : 0.0f;
+      q = make_float4(m * (gx * inv), m * (gy * inv), m * (gz * inv), m + m2);
     }
     if constexpr (NS) {
       ngs[n1 * NTX + t] = q;
@@ -130,14 +138,11 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
       mm[n1] = q.w;
     }
   }
-  const long long rows_per_field = (long long)g.nz * g.ny;
-  const int nrot = (int)(nrows / rows_per_field);
   // Masks are paired across consecutive rotations: the even rotation's mask
   // field carries (M_r, M_{r+1}); an odd rotation has no mask field of its own.
   const bool odd_block = ((blockIdx.x * (long long)ROWS) / rows_per_field & 1) &&
                          (blockIdx.x * (long long)ROWS) / rows_per_field ==
                              (min(blockIdx.x * (long long)ROWS + ROWS, nrows) - 1) / rows_per_field;
-  const bool has_partner = !(r & 1) && r + 1 < nrot;
 #pragma unroll 1
   for (int j = 0; j < g.nf; ++j) {
     if (j == g.nch && odd_block) break;          // uniform over the block
@@ -145,30 +150,37 @@ k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __re
     // mask field comes last
     const int code = j == g.nch ? 3 : (g.nch == 3 ? j : 4 + j);
     float2 v[H];
+    // this field's inputs, with the field's product chosen at compile time
+    auto inputs = [&](auto cc) {
+      constexpr int CODE = decltype(cc)::value;
 #pragma unroll
-    for (int n1 = 0; n1 < H; ++n1) {
-      float X, Y, Z, m;
-      if constexpr (NS) {
-        const float4 q = ngs[n1 * NTX + t];     // this thread's own slot
-        X = q.x; Y = q.y; Z = q.z; m = q.w;
-      } else {
-        X = vx[n1 < HR ? n1 : 0]; Y = vy[n1 < HR ? n1 : 0]; Z = vz[n1 < HR ? n1 : 0];
-        m = mm[n1 < HR ? n1 : 0];
-      }
-      switch (code) {
-        case 0: v[n1] = make_float2(m * X * X, m * Y * Y); break;
-        case 1: v[n1] = make_float2(m * Z * Z, m * X * Y); break;
-        case 2: v[n1] = make_float2(m * X * Z, m * Y * Z); break;
-        case 4: v[n1] = make_float2(m * X, m * Y); break;
-        case 5: v[n1] = make_float2(m * Z, 0.0f); break;
-        default: {
-          const int x = N2 * n1 + n2;
-          float m2 = 0.0f;
-          if (has_partner && row_ok && x < g.nx) m2 = M[g.nvox + base + x] ? 1.0f : 0.0f;
-          v[n1] = (r & 1) ? make_float2(0.0f, 0.0f) : make_float2(m, m2);
-          break;
+      for (int n1 = 0; n1 < H; ++n1) {
+        float X, Y, Z, w;
+        if constexpr (NS) {
+          const float4 q = ngs[n1 * NTX + t];   // this thread's own slot
+          X = q.x; Y = q.y; Z = q.z; w = q.w;
+        } else {
+          X = vx[n1 < HR ? n1 : 0]; Y = vy[n1 < HR ? n1 : 0]; Z = vz[n1 < HR ? n1 : 0];
+          w = mm[n1 < HR ? n1 : 0];
+        }
+        if constexpr (CODE == 0) v[n1] = make_float2(X * X, Y * Y);
+        else if constexpr (CODE == 1) v[n1] = make_float2(Z * Z, X * Y);
+        else if constexpr (CODE == 2) v[n1] = make_float2(X * Z, Y * Z);
+        else if constexpr (CODE == 4) v[n1] = make_float2(X, Y);
+        else if constexpr (CODE == 5) v[n1] = make_float2(Z, 0.0f);
+        else {                                   // mask pair (M_r, M_{r+1}); w = m + 2 m2
+          const float m2 = w >= 2.0f ? 1.0f : 0.0f;
+          v[n1] = (r & 1) ? make_float2(0.0f, 0.0f) : make_float2(w - 2.0f * m2, m2);
         }
       }
+    };
+    switch (code) {
+      case 0: inputs(std::integral_constant<int, 0>{}); break;
+      case 1: inputs(std::integral_constant<int, 1>{}); break;
+      case 2: inputs(std::integral_constant<int, 2>{}); break;
+      case 4: inputs(std::integral_constant<int, 4>{}); break;
+      case 5: inputs(std::integral_constant<int, 5>{}); break;
+      default: inputs(std::integral_constant<int, 3>{}); break;
     }
     FI::template step1<-1>(v, ex + lrow * CS, n2, tw);
     __syncthreads();
