@@ -421,6 +421,19 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": total_bytes / (prof_steps * nbatches),
                 "timing": "CUDA events around every launch of one profiled step after the timed region"}
 
+    # the whole step against HBM: the ncu DRAM bytes per rotation of every
+    # scoring stage (same kernel sources and precision only), times the
+    # rotations, over the timed step
+    step_bytes = [ncu_traffic(st, args.precision) for st in ("resample", "fwd_x", "fwd_y", "zmac",
+                                                            "inv_y", "inv_x")]
+    roofline_step = None
+    if all(b is not None for b in step_bytes):
+        per_rot = sum(step_bytes)
+        ach = per_rot * R / (elapsed_ms / args.steps / 1000.0) / 1e9
+        roofline_step = {"bound": "hbm", "dram_bytes_per_rotation": per_rot, "achieved": ach,
+                         "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "note": "ncu DRAM bytes of all scoring stages per rotation x rotations / step time"}
+
     roofline_alu = None
     if dom == "zmac":
         fl = sum(zmac_flops(dims, cp, nb) for cp, nb in launches_of) * prof_steps
@@ -457,7 +470,7 @@ def run_ours(args):
                        "rotations_per_gpu": R, "batch": f.batch, "masks": "thresholded foreground",
                        "l2": "inputs larger than L2: every step streams >1 TB of FFT intermediates",
                        "step": "update_fixed + score all rotations + max over rotations"},
-            "roofline": roofline, "roofline_alu": roofline_alu,
+            "roofline": roofline, "roofline_alu": roofline_alu, "roofline_step": roofline_step,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * R * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

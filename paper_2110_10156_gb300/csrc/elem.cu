@@ -97,9 +97,9 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
   val = 0.0f;
   m = 0;
   if (ax.inside && ay.inside && az.inside) {
-    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-    const long long b000 = (long long)az.i0 * sz + (long long)ay.i0 * sy + ax.i0;
-    const long long o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+    const int sy = g.nx, sz = g.nx * g.ny;        // volumes hold < 2^31 voxels
+    const int b000 = az.i0 * sz + ay.i0 * sy + ax.i0;
+    const int o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
     float2 c[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) c[k] = __ldg(&BM[b000 + o[k]]);
@@ -109,12 +109,18 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
     float v10 = lerp_exact(c[4].x, c[5].x, ax.t), v11 = lerp_exact(c[6].x, c[7].x, ax.t);
     float v0 = lerp_exact(v00, v01, ay.t), v1 = lerp_exact(v10, v11, ay.t);
     val = lerp_exact(v0, v1, az.t);
-    // mask decision: same lerp order, round-to-nearest, no contraction
-    float m00 = lerp_rn(c[0].y, c[1].y, ax.t), m01 = lerp_rn(c[2].y, c[3].y, ax.t);
-    float m10 = lerp_rn(c[4].y, c[5].y, ax.t), m11 = lerp_rn(c[6].y, c[7].y, ax.t);
-    float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
-    float mm = lerp_rn(m0, m1, az.t);
-    m = (mm >= 0.5f) ? 1 : 0;
+    // mask decision: same lerp order, round-to-nearest, no contraction; when
+    // the eight corners agree every lerp returns their value exactly
+    const float msum = ((c[0].y + c[1].y) + (c[2].y + c[3].y)) + ((c[4].y + c[5].y) + (c[6].y + c[7].y));
+    if (msum == 0.0f || msum == 8.0f) {
+      m = msum == 8.0f ? 1 : 0;
+    } else {
+      float m00 = lerp_rn(c[0].y, c[1].y, ax.t), m01 = lerp_rn(c[2].y, c[3].y, ax.t);
+      float m10 = lerp_rn(c[4].y, c[5].y, ax.t), m11 = lerp_rn(c[6].y, c[7].y, ax.t);
+      float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
+      float mm = lerp_rn(m0, m1, az.t);
+      m = (mm >= 0.5f) ? 1 : 0;
+    }
   }
 }
 

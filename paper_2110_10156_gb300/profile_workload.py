@@ -69,7 +69,8 @@ def traffic_from_csv(csv_path: str, rotations: int, out_path: str, precision: st
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--traffic-from", help="summarise an ncu CSV log into profiles/ncu_traffic.json")
-    ap.add_argument("--precision", choices=("fp32", "bf16"), default="fp32")
+    ap.add_argument("--traffic-out", help="write the summary here instead")
+    ap.add_argument("--precision", choices=("fp32", "bf16", "fp16"), default="fp32")
     ap.add_argument("--pad-mode", choices=("bound", "full"), default="bound")
     ap.add_argument("--size", type=int, default=150)
     ap.add_argument("--rotations", type=int, default=2)
@@ -81,7 +82,8 @@ def main(argv=None) -> int:
         import os
         root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
         out = traffic_from_csv(args.traffic_from, args.rotations,
-                               os.path.join(root, "profiles", "ncu_traffic.json"), args.precision)
+                               args.traffic_out or os.path.join(root, "profiles", "ncu_traffic.json"),
+                               args.precision)
         print(json.dumps(out, indent=1))
         return 0
 
