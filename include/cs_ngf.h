@@ -416,6 +416,21 @@ typedef struct {
 int32_t cs_ngf_tuning(int32_t cap, cs_ngf_tuning_entry* out);
 void cs_ngf_tuning_reset(void);
 
+/* The length classes bound-limited padding forms, computed on the host
+ * alone (what a scoring call does after counting the rotated masks):
+ *   dims     {nz, ny, nx}; max_pad the largest lengths (each >= 2n - 1)
+ *   cur_pad  the lengths in use (their class is scored first) or NULL
+ *   bounds   [R][6] per rotation the admitted shift slots v = chi + n - 1,
+ *            {lo_z, hi_z, lo_y, hi_y, lo_x, hi_x} (lo > hi: none on that axis)
+ * Each rotation needs per axis the shortest supported length
+ * P >= n + max(n - 1 - lo, hi - (n - 1)).  Fills up to cap entries of pads
+ * [cap][3] and counts [cap], and order [R] with the rotations in class order
+ * (each may be NULL); returns the number of classes, or -1 for bad arguments.
+ * No device is touched. */
+int32_t cs_ngf_plan_lengths(const int32_t dims[3], const int32_t max_pad[3], const int32_t cur_pad[3],
+                            int32_t R, const int32_t* bounds, int32_t cap, int32_t* pads,
+                            int32_t* counts, int32_t* order);
+
 /* Free every device allocation of the handle (NULL is a no-op).  The caller
  * makes sure no work that uses the handle is still in flight. */
 void cs_ngf_release(cs_ngf_fixed* f);

@@ -32,7 +32,7 @@ EXPORTED = (
     "cs_ngf_server_default_config", "cs_ngf_server_create", "cs_ngf_server_submit",
     "cs_ngf_server_cancel", "cs_ngf_server_wait", "cs_ngf_server_stats", "cs_ngf_server_destroy",
     "cs_ngf_search_default_config", "cs_ngf_global_align", "cs_ngf_length_sets",
-    "cs_ngf_tuning", "cs_ngf_tuning_reset",
+    "cs_ngf_tuning", "cs_ngf_tuning_reset", "cs_ngf_plan_lengths",
 )
 
 MAX_LEVELS = 8
@@ -115,6 +115,10 @@ _lib.cs_ngf_status_string.argtypes = [_i32]
 _lib.cs_ngf_status_string.restype = ctypes.c_char_p
 _lib.cs_ngf_last_error.argtypes = []
 _lib.cs_ngf_last_error.restype = ctypes.c_char_p
+_lib.cs_ngf_plan_lengths.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _i32,
+                                     ctypes.c_void_p, _i32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]
+_lib.cs_ngf_plan_lengths.restype = _i32
 _lib.cs_ngf_tuning.argtypes = [_i32, ctypes.c_void_p]
 _lib.cs_ngf_tuning.restype = _i32
 _lib.cs_ngf_tuning_reset.argtypes = []
@@ -176,6 +180,24 @@ def library():
 def launch_count() -> int:
     """Kernel launches made by the library in this process."""
     return int(_lib.cs_ngf_launch_count())
+
+
+def plan_lengths(dims, max_pad, bounds, cur_pad=None):
+    """Length classes of bound-limited padding for per-rotation shift bounds
+    [R][6] (cs_ngf_plan_lengths, host only): ([((Pz, Py, Px), count)], order)."""
+    b = np.ascontiguousarray(bounds, dtype=np.int32).reshape(-1, 6)
+    R = b.shape[0]
+    d = (ctypes.c_int32 * 3)(*dims)
+    m = (ctypes.c_int32 * 3)(*max_pad)
+    c = (ctypes.c_int32 * 3)(*cur_pad) if cur_pad is not None else None
+    pads = (ctypes.c_int32 * 24)()
+    counts = (ctypes.c_int32 * 8)()
+    order = np.zeros(R, np.int32)
+    n = int(_lib.cs_ngf_plan_lengths(d, m, c, R, b.ctypes.data_as(ctypes.c_void_p), 8, pads, counts,
+                                     order.ctypes.data_as(ctypes.c_void_p)))
+    if n < 0:
+        raise CsNgfError(EINVAL, "cs_ngf_plan_lengths")
+    return [((pads[3 * k], pads[3 * k + 1], pads[3 * k + 2]), int(counts[k])) for k in range(n)], order
 
 
 def tuning():

@@ -622,12 +622,11 @@ cs_ngf_status rotation_bounds(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStr
 
 // FFT lengths one rotation needs: per axis the shortest supported P >=
 // n + max(-chi_lo, chi_hi) over its admitted shifts; false if it admits none
-bool rotation_lengths(const cs_ngf_fixed* f, const int* b, int pad[3]) {
-  const int dims[3] = {f->g.nz, f->g.ny, f->g.nx};
+bool rotation_lengths(const int dims[3], const int max_pad[3], const int* b, int pad[3]) {
   if (b[0] > b[1] || b[2] > b[3] || b[4] > b[5]) return false;
   for (int a = 0; a < 3; ++a) {
     const int n = dims[a], lo = b[2 * a], hi = b[2 * a + 1];
-    pad[a] = length_for(n + std::max(n - 1 - lo, hi - (n - 1)), f->alloc_pad[a]);
+    pad[a] = length_for(n + std::max(n - 1 - lo, hi - (n - 1)), max_pad[a]);
   }
   return true;
 }
@@ -679,12 +678,16 @@ struct LengthClass { int pad[3]; std::vector<int> rot; };
 
 double class_volume(const int* p) { return (double)p[0] * p[1] * p[2]; }
 
-std::vector<LengthClass> length_classes(const cs_ngf_fixed* f, int R) {
+// dims, max_pad: the volume and the largest lengths; cur: the lengths in use
+// (their class goes first); bounds [R][6]: each rotation's admitted shift
+// slots {lo_z, hi_z, lo_y, hi_y, lo_x, hi_x}
+std::vector<LengthClass> length_classes(const int dims[3], const int max_pad[3], const int cur[3],
+                                        int R, const int* bounds) {
   std::vector<LengthClass> cls;
   std::vector<int> none;
   for (int r = 0; r < R; ++r) {
     int p[3];
-    if (!rotation_lengths(f, f->allb_h + 6 * (size_t)r, p)) { none.push_back(r); continue; }
+    if (!rotation_lengths(dims, max_pad, bounds + 6 * (size_t)r, p)) { none.push_back(r); continue; }
     size_t k = 0;
     while (k < cls.size() && !std::equal(p, p + 3, cls[k].pad)) ++k;
     if (k == cls.size()) cls.push_back({{p[0], p[1], p[2]}, {}});
@@ -716,15 +719,13 @@ std::vector<LengthClass> length_classes(const cs_ngf_fixed* f, int R) {
   }
   if (cls.empty()) {
     LengthClass lc;
-    for (int a = 0; a < 3; ++a) lc.pad[a] = length_for(a == 0 ? f->g.nz : a == 1 ? f->g.ny : f->g.nx,
-                                                       f->alloc_pad[a]);
+    for (int a = 0; a < 3; ++a) lc.pad[a] = length_for(dims[a], max_pad[a]);
     cls.push_back(lc);
   }
   cls[0].rot.insert(cls[0].rot.end(), none.begin(), none.end());
   std::sort(cls[0].rot.begin(), cls[0].rot.end());
   // start with the lengths in use (no recomputation), then the larger classes
   std::stable_sort(cls.begin(), cls.end(), [&](const LengthClass& a, const LengthClass& b) {
-    const int cur[3] = {f->g.Pz, f->g.Py, f->g.Px};
     const bool ca = std::equal(a.pad, a.pad + 3, cur), cb = std::equal(b.pad, b.pad + 3, cur);
     if (ca != cb) return ca;
     return a.rot.size() > b.rot.size();
@@ -748,7 +749,8 @@ cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream
   f->last_counts.assign(1, R);
   if (f->pad_mode != CS_NGF_PAD_BOUND) return CS_NGF_OK;
   if (cs_ngf_status s = rotation_bounds(f, MB, R, st)) return s;
-  std::vector<LengthClass> cls = length_classes(f, R);
+  const int dims[3] = {f->g.nz, f->g.ny, f->g.nx}, cur[3] = {f->g.Pz, f->g.Py, f->g.Px};
+  std::vector<LengthClass> cls = length_classes(dims, f->alloc_pad, cur, R, f->allb_h);
   f->length_sets = (int)cls.size();
   ends.clear();
   pads.clear();
@@ -1132,6 +1134,29 @@ cs_ngf_status cs_ngf_get_info(const cs_ngf_fixed* f, cs_ngf_info* info) {
 }
 
 void cs_ngf_release(cs_ngf_fixed* f) { free_handle(f); }
+
+int32_t cs_ngf_plan_lengths(const int32_t dims[3], const int32_t max_pad[3], const int32_t cur_pad[3],
+                            int32_t R, const int32_t* bounds, int32_t cap, int32_t* pads,
+                            int32_t* counts, int32_t* order) {
+  if (!dims || !max_pad || R <= 0 || !bounds) return -1;
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 2 || dims[a] > 256 || !pad_supported(max_pad[a]) || max_pad[a] < 2 * dims[a] - 1)
+      return -1;
+  const int d[3] = {dims[0], dims[1], dims[2]}, m[3] = {max_pad[0], max_pad[1], max_pad[2]};
+  const int c[3] = {cur_pad ? cur_pad[0] : 0, cur_pad ? cur_pad[1] : 0, cur_pad ? cur_pad[2] : 0};
+  const std::vector<LengthClass> cls = length_classes(d, m, c, R, bounds);
+  int k = 0;
+  for (size_t i = 0; i < cls.size(); ++i) {
+    if ((int)i < cap) {
+      if (pads)
+        for (int a = 0; a < 3; ++a) pads[3 * i + a] = cls[i].pad[a];
+      if (counts) counts[i] = (int32_t)cls[i].rot.size();
+    }
+    if (order)
+      for (int r : cls[i].rot) order[k++] = r;
+  }
+  return (int32_t)cls.size();
+}
 
 int32_t cs_ngf_tuning(int32_t cap, cs_ngf_tuning_entry* out) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
