@@ -130,7 +130,9 @@ typedef struct {
                         (cs_ngf_tuning lists the choices).  Every split computes the same
                         transform; results differ from the default only by FP32 rounding,
                         and are reproducible within a process, not across processes
-                        whose timings choose differently. */
+                        whose timings choose differently.
+                        2: every pass uses the alternative split wherever its length has
+                        one, without timing (for tests and comparisons). */
 } cs_ngf_config;
 
 typedef struct {

@@ -248,6 +248,9 @@ class Fixed:
 
     def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None,
                  measure="squared", precision="fp32", pad_mode="bound", autotune=False):
+        """autotune: False (built-in radix splits), True (timed on first use
+        at new lengths) or "alternative" (the second split wherever a length
+        has one)."""
         import torch
         if A.dim() != 3:
             raise ValueError("A must be [nz][ny][nx]")
@@ -265,7 +268,7 @@ class Fixed:
         cfg.measure = MEASURES[measure]
         cfg.precision = PRECISIONS[precision]
         cfg.pad_mode = PAD_MODES[pad_mode]
-        cfg.autotune = 1 if autotune else 0
+        cfg.autotune = 2 if autotune == "alternative" else (1 if autotune else 0)
         self.measure = measure
         self.precision = precision
         self.pad_mode = pad_mode

@@ -299,12 +299,17 @@ TuneKey tune_key(const cs_ngf_fixed* f, int k) {
 }
 
 // the variants the handle uses at its lengths in use: the table's choices
-// when autotuning, else the built-in splits
+// when autotuning, the alternative wherever there is one in mode 2, else the
+// built-in splits
 void resolve_variants(cs_ngf_fixed* f) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (int k = 0; k < kPasses; ++k) {
     f->vars[k] = 0;
-    if (!f->autotune) continue;
+    if (f->autotune == 2) {
+      f->vars[k] = has_alt_split(tune_key(f, k).P) ? 1 : 0;
+      continue;
+    }
+    if (f->autotune != 1) continue;
     auto it = g_tune.find(tune_key(f, k));
     if (it != g_tune.end()) f->vars[k] = it->second.variant;
   }
@@ -312,7 +317,7 @@ void resolve_variants(cs_ngf_fixed* f) {
 
 // some pass at the lengths in use has two splits and no choice yet
 bool needs_tuning(const cs_ngf_fixed* f) {
-  if (!f->autotune) return false;
+  if (f->autotune != 1) return false;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (int k = 0; k < kPasses; ++k) {
     const TuneKey key = tune_key(f, k);
@@ -814,7 +819,7 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
     return fail(CS_NGF_EINVAL, "unknown precision");
   if (cfg.pad_mode != CS_NGF_PAD_FULL && cfg.pad_mode != CS_NGF_PAD_BOUND)
     return fail(CS_NGF_EINVAL, "unknown pad_mode");
-  if (cfg.autotune != 0 && cfg.autotune != 1) return fail(CS_NGF_EINVAL, "autotune must be 0 or 1");
+  if (cfg.autotune < 0 || cfg.autotune > 2) return fail(CS_NGF_EINVAL, "autotune must be 0, 1 or 2");
   for (int a = 0; a < 3; ++a) {
     pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
     if (!pad_supported(pad[a]))
@@ -960,7 +965,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   set_field_scales(g);
   for (int a = 0; a < 3; ++a) f->alloc_pad[a] = pad[a];
   f->pad_mode = cfg.pad_mode;
-  f->autotune = cfg.autotune != 0;
+  f->autotune = cfg.autotune;
   resolve_variants(f);
 
   const Sizes sz = sizes_for(dims, pad, cfg.measure, cfg.precision);

@@ -37,8 +37,9 @@ struct cs_ngf_fixed {
   std::vector<int> last_pads;  // their lengths [3 per set] and rotation counts
   std::vector<int> last_counts;
   // split variant of each FFT pass at the lengths in use (fwd_x, fwd_y, zmac,
-  // inv_y, inv_x): 0 unless autotuning chose the alternative
-  bool autotune = false;
+  // inv_y, inv_x): 0 unless autotuning chose the alternative (autotune 1) or
+  // the alternatives are requested outright (autotune 2)
+  int autotune = 0;
   int vars[5] = {0, 0, 0, 0, 0};
   int gexec_vars[5] = {0, 0, 0, 0, 0};   // the variants gexec was captured with
   // one captured graph per set of FFT lengths (all reference the same buffers)

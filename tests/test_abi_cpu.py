@@ -73,7 +73,7 @@ def test_prepare_rejects_bad_arguments_before_touching_the_device(binding):
     assert b"pad_mode" in lib.cs_ngf_last_error()
     cfg.pad_mode = binding.PAD_MODES["full"]
     assert cfg.autotune == 0
-    cfg.autotune = 2
+    cfg.autotune = 3
     assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None, ctypes.byref(h)) == binding.EINVAL
     assert b"autotune" in lib.cs_ngf_last_error()
     cfg.autotune = 1

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import cs_ngf_oracle as O
 from paper_2110_10156_gb300 import synth
-from tests.parity_util import TAU_FP32, check_best_against_map
+from tests.parity_util import TAU_FP32, check_best_against_map, check_maps
 
 pytestmark = pytest.mark.gpu
 
@@ -75,6 +75,36 @@ def test_autotune_with_bound_limited_lengths(cs):
     lengths = {ln for cp, _ in f.length_classes() for ln in cp}
     timed = {e["length"] for e in cs.tuning()}
     assert {ln for ln in lengths if ln in ALT} <= timed
+    for r, q in enumerate(p.quats):
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q)
+        check_best_against_map(omap, sc[r], sh[r])
+
+
+@pytest.mark.parametrize("P", sorted(ALT))
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_every_alternative_split_matches_oracle(cs, P, axis):
+    """Each length's second split on one axis at a time (z: the z pass; y: the
+    y forward and inverse passes; x: the x forward and inverse passes), full
+    padding so that the length is the requested one, against the oracle."""
+    dims = (7, 8, 6)
+    pad = [16, 16, 16]
+    pad[axis] = P
+    p = synth.small_pair(900 + P + axis, dims, masks="threshold", n_rot=2)
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), pad=tuple(pad), pad_mode="full", autotune="alternative")
+    for q in (p.q_true, p.quats[-1]):
+        gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, pad=tuple(pad))
+        check_maps(omap, gmap)
+    f.release()
+
+
+def test_alternative_splits_with_full_length_inputs(cs):
+    """Bound-limited lengths shorter than twice the side, so that the forward
+    passes read full-length inputs, with every alternative split."""
+    p = synth.small_pair(21, (30, 30, 30), masks="threshold", n_rot=24)
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), batch=4, autotune="alternative")
+    sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
+    assert any(ln in ALT for cp, _ in f.length_classes() for ln in cp)
     for r, q in enumerate(p.quats):
         omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q)
         check_best_against_map(omap, sc[r], sh[r])
