@@ -166,7 +166,8 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->UV);
   cudaFree(f->Bh);
   cudaFree(f->Mh);
-  cudaFree(f->BM);
+  cudaFree(f->BP);
+  cudaFree(f->C8);
   cudaFree(f->F02);
   cudaFree(f->F13);
   cudaFree(f->msum);
@@ -399,14 +400,14 @@ cs_ngf_status run_transforms(cs_ngf_fixed* f, int nb, float* map, cudaStream_t s
   return CS_NGF_OK;
 }
 
-// (B, M_B) -> f->BM, shared by every rotation of the call
+// (B, M_B) -> f->BP, f->C8, shared by every rotation of the call
 cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st) {
-  { Stage sp(f, 0, st); k_pack_bm<<<512, 256, 0, st>>>(B, MB, f->g.nvox, f->BM); }
+  { Stage sp(f, 0, st); k_pack_floating<<<512, 256, 0, st>>>(B, MB, f->g, f->BP, f->C8); }
   return check_launch("pack");
 }
 
 // score nb rotations whose matrices are at rot (device), with the floating
-// volume already packed in f->BM; results to out_score[nb], out_shift[nb][3]
+// volume already packed in f->BP, f->C8; results to out_score[nb], out_shift[nb][3]
 cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float* out_score,
                                int32_t* out_shift, float* map, cudaStream_t st, bool tune = false) {
   const Geo& g = f->g;
@@ -416,7 +417,7 @@ cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float
   CS_CUDA(cudaMemsetAsync(f->margB, 0, sizeof(int) * nmarg * nb, st));
   {
     Stage sp(f, 0, st);
-    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BM, rot, g, f->Bh, f->Mh, f->msum, f->margB);
+    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BP, f->C8, rot, g, f->Bh, f->Mh, f->msum, f->margB);
   }
   if (cs_ngf_status s = check_launch("resample")) return s;
   const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
@@ -598,9 +599,9 @@ cs_ngf_status ensure_rotation_buffers(cs_ngf_fixed* f, int R) {
 }
 
 // Section 3.2 shift bounds of each of the R uploaded rotations (the same
-// counts and bound the launch groups compute) into f->allb_h [R][6];
-// synchronises st
-cs_ngf_status rotation_bounds(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st) {
+// counts and bound the launch groups compute, from the floating volume
+// pack_floating prepared) into f->allb_h [R][6]; synchronises st
+cs_ngf_status rotation_bounds(cs_ngf_fixed* f, int R, cudaStream_t st) {
   if (cs_ngf_status s = ensure_rotation_buffers(f, R)) return s;
   const Geo& g = f->g;
   const size_t nmarg = (size_t)g.nz + g.ny + g.nx;
@@ -610,7 +611,7 @@ cs_ngf_status rotation_bounds(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStr
     CS_CUDA(cudaMemsetAsync(f->margB, 0, sizeof(int) * nmarg * nb, st));
     {
       Stage sp(f, 0, st);
-      k_mask_counts<<<resample_grid(g, nb), 128, 0, st>>>(MB, f->rot_d + r0, g, f->msum, f->margB);
+      k_mask_counts<<<resample_grid(g, nb), 128, 0, st>>>(f->C8, f->rot_d + r0, g, f->msum, f->margB);
     }
     if (cs_ngf_status s = check_launch("mask counts")) return s;
     {
@@ -738,13 +739,14 @@ std::vector<LengthClass> length_classes(const int dims[3], const int max_pad[3],
   return cls;
 }
 
-// Length classes of the R uploaded rotations (floating mask MB, device):
+// Length classes of the R uploaded rotations (floating volume packed by
+// pack_floating):
 // bounds (synchronises st), classes, and the rotation matrices re-uploaded
 // in class order when there is more than one.  perm[i] = original index of
 // the i-th rotation in class order (empty if the order is unchanged); class
 // c covers [ends[c-1], ends[c]) with lengths pads[c].  Without bound-limited
 // padding: one class with the lengths in use.
-cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st,
+cs_ngf_status plan_classes(cs_ngf_fixed* f, int R, cudaStream_t st,
                            std::vector<int>& perm, std::vector<int>& ends, std::vector<int>& pads) {
   perm.clear();
   ends.assign(1, R);
@@ -753,7 +755,7 @@ cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream
   f->last_pads = pads;
   f->last_counts.assign(1, R);
   if (f->pad_mode != CS_NGF_PAD_BOUND) return CS_NGF_OK;
-  if (cs_ngf_status s = rotation_bounds(f, MB, R, st)) return s;
+  if (cs_ngf_status s = rotation_bounds(f, R, st)) return s;
   const int dims[3] = {f->g.nz, f->g.ny, f->g.nx}, cur[3] = {f->g.Pz, f->g.Py, f->g.Px};
   std::vector<LengthClass> cls = length_classes(dims, f->alloc_pad, cur, R, f->allb_h);
   f->length_sets = (int)cls.size();
@@ -787,7 +789,7 @@ cs_ngf_status score_all(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cons
   if (cs_ngf_status s = upload_rotations(f, quats, R, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, MB, st)) return s;
   std::vector<int> perm, ends, pads;
-  if (cs_ngf_status s = plan_classes(f, MB, R, st, perm, ends, pads)) return s;
+  if (cs_ngf_status s = plan_classes(f, R, st, perm, ends, pads)) return s;
   if (perm.empty()) {
     if (cs_ngf_status s = set_pads(f, pads.data(), st)) return s;
     return score_range_impl(f, 0, R, best_score, best_shift, st);
@@ -851,7 +853,7 @@ Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure, int precis
   z.fixed_f02 = nf * E0;                                            // one rotation, FP32 (A side)
   z.fixed_f13 = nf * E1;
   z.per_rot = (z.f02_elems + z.f13_elems) * sizeof(float2) + nvox * 5;
-  z.shared_ws = nvox * sizeof(float2);
+  z.shared_ws = nvox * (sizeof(float2) + 1);                       // BP, C8
   z.uv_elems = (2 * nch + 1) * (Px / 2 + 1) * Py * Pz;
   return z;
 }
@@ -884,9 +886,9 @@ cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int
                           cudaStream_t st) {
   return ::score_range_impl(f, r0, n, best_score, best_shift, st);
 }
-cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st,
+cs_ngf_status plan_classes(cs_ngf_fixed* f, int R, cudaStream_t st,
                            std::vector<int>& perm, std::vector<int>& ends, std::vector<int>& pads) {
-  return ::plan_classes(f, MB, R, st, perm, ends, pads);
+  return ::plan_classes(f, R, st, perm, ends, pads);
 }
 cs_ngf_status set_lengths(cs_ngf_fixed* f, const int pad[3], cudaStream_t st) {
   return ::set_pads(f, pad, st);
@@ -996,7 +998,8 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->UV, uv_elems));
   CS_TRYC(dalloc(&f->Bh, (size_t)batch * g.nvox));
   CS_TRYC(dalloc(&f->Mh, (size_t)batch * g.nvox));
-  CS_TRYC(dalloc(&f->BM, (size_t)g.nvox));
+  CS_TRYC(dalloc(&f->BP, (size_t)g.nvox));
+  CS_TRYC(dalloc(&f->C8, (size_t)g.nvox));
   CS_TRYC(dalloc(&f->F02, std::max((size_t)batch * f->f02_elems, sz.fixed_f02)));
   CS_TRYC(dalloc(&f->F13, std::max((size_t)batch * f->f13_elems, sz.fixed_f13)));
   CS_TRYC(dalloc(&f->msum, (size_t)batch));
@@ -1103,7 +1106,7 @@ cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* m
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
   std::vector<int> perm, ends, pads;
-  if (cs_ngf_status s = plan_classes(f, maskB, 1, st, perm, ends, pads)) return s;
+  if (cs_ngf_status s = plan_classes(f, 1, st, perm, ends, pads)) return s;
   if (cs_ngf_status s = set_pads(f, pads.data(), st)) return s;
   return score_batch(f, 0, 1, f->res_score, f->res_shift, map, st);
 }
@@ -1119,7 +1122,7 @@ cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* ma
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
   const Geo& g = f->g;
   if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
-  k_resample<<<resample_grid(g, 1), 128, 0, st>>>(f->BM, f->rot_d, g, Bhat, Mhat, f->msum, nullptr);
+  k_resample<<<resample_grid(g, 1), 128, 0, st>>>(f->BP, f->C8, f->rot_d, g, Bhat, Mhat, f->msum, nullptr);
   return check_launch("resample");
 }
 

@@ -35,13 +35,28 @@ __device__ __forceinline__ float lerp_rn(float a, float b, float t) {
 }
 }  // namespace
 
-// B and its mask packed as (value, 0/1) pairs, so each trilinear corner is
-// one 8-byte load (the volume is shared by every rotation of a call)
-__global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict__ MB, long long n,
-                          float2* __restrict__ BM) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    BM[i] = make_float2(B[i], MB[i] ? 1.0f : 0.0f);
+// The floating volume as the resample reads it, prepared once per call and
+// shared by every rotation: x-pairs BP[i] = (B[i], B[i+1]), so the two x
+// corners of a cell come in one 8-byte load, and corner codes C8[i] whose bit
+// k is M_B at corner (dx, dy, dz) = (k & 1, (k >> 1) & 1, k >> 2) of the cell
+// with base voxel i, so the eight mask corners come in one byte.  A cell base
+// is never on a far face (axis_sample clamps i0 <= n - 2); those entries hold 0.
+__global__ void k_pack_floating(const float* __restrict__ B, const uint8_t* __restrict__ MB, Geo g,
+                                float2* __restrict__ BP, uint8_t* __restrict__ C8) {
+  const int sy = g.nx, sz = g.nx * g.ny;          // volumes hold < 2^31 voxels
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.nvox;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / sz);
+    const bool in_x = x + 1 < g.nx;
+    BP[i] = make_float2(B[i], in_x ? B[i + 1] : 0.0f);
+    unsigned bits = 0;
+    if (in_x && y + 1 < g.ny && z + 1 < g.nz) {
+      const int o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bits |= (MB[i + o[k]] ? 1u : 0u) << k;
+    }
+    C8[i] = (uint8_t)bits;
+  }
 }
 
 // sample point p = R (x - c) + c of voxel (x, y, z) per axis (FP32, fixed order)
@@ -64,32 +79,33 @@ __device__ __forceinline__ void sample_axes(const RotMat& R, const Geo& g, int x
   az = axis_sample(p[2], g.nz);
 }
 
-// the rotated mask alone, from the 0/1 bytes of M_B: the same sample point
-// and the same lerp sequence as resample_voxel, so the same decision
-__device__ __forceinline__ uint8_t mask_voxel(const uint8_t* __restrict__ MB, const RotMat& R,
-                                              const Geo& g, int x, int y, int z) {
-  AxisSample ax, ay, az;
-  sample_axes(R, g, x, y, z, ax, ay, az);
-  if (!(ax.inside && ay.inside && az.inside)) return 0;
-  const int sy = g.nx, sz = g.nx * g.ny;          // volumes hold < 2^31 voxels
-  const int b000 = az.i0 * sz + ay.i0 * sy + ax.i0;
-  const int o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
-  unsigned bits = 0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) bits |= (__ldg(&MB[b000 + o[k]]) ? 1u : 0u) << k;
-  // equal corners: every lerp a + t (a - a) returns a exactly
+// the mask decision [trilinear M_B >= 0.5] from the cell's corner code: lerps
+// along x, y, z in round-to-nearest FP32 with no contraction; when the eight
+// corners agree every lerp a + t (a - a) returns a exactly
+__device__ __forceinline__ uint8_t mask_decision(unsigned bits, float tx, float ty, float tz) {
   if (bits == 0u) return 0;
   if (bits == 0xffu) return 1;
   float c[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) c[k] = ((bits >> k) & 1u) ? 1.0f : 0.0f;
-  float m00 = lerp_rn(c[0], c[1], ax.t), m01 = lerp_rn(c[2], c[3], ax.t);
-  float m10 = lerp_rn(c[4], c[5], ax.t), m11 = lerp_rn(c[6], c[7], ax.t);
-  float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
-  return lerp_rn(m0, m1, az.t) >= 0.5f ? 1 : 0;
+  const float m00 = lerp_rn(c[0], c[1], tx), m01 = lerp_rn(c[2], c[3], tx);
+  const float m10 = lerp_rn(c[4], c[5], tx), m11 = lerp_rn(c[6], c[7], tx);
+  const float m0 = lerp_rn(m00, m01, ty), m1 = lerp_rn(m10, m11, ty);
+  return lerp_rn(m0, m1, tz) >= 0.5f ? 1 : 0;
 }
 
-__device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, const RotMat& R,
+// the rotated mask alone: the same sample point and decision as resample_voxel
+__device__ __forceinline__ uint8_t mask_voxel(const uint8_t* __restrict__ C8, const RotMat& R,
+                                              const Geo& g, int x, int y, int z) {
+  AxisSample ax, ay, az;
+  sample_axes(R, g, x, y, z, ax, ay, az);
+  if (!(ax.inside && ay.inside && az.inside)) return 0;
+  const int b000 = az.i0 * (g.nx * g.ny) + ay.i0 * g.nx + ax.i0;
+  return mask_decision(__ldg(&C8[b000]), ax.t, ay.t, az.t);
+}
+
+__device__ __forceinline__ void resample_voxel(const float2* __restrict__ BP,
+                                               const uint8_t* __restrict__ C8, const RotMat& R,
                                                const Geo& g, int x, int y, int z, float& val,
                                                uint8_t& m) {
   AxisSample ax, ay, az;
@@ -99,28 +115,16 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
   if (ax.inside && ay.inside && az.inside) {
     const int sy = g.nx, sz = g.nx * g.ny;        // volumes hold < 2^31 voxels
     const int b000 = az.i0 * sz + ay.i0 * sy + ax.i0;
-    const int o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
-    float2 c[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) c[k] = __ldg(&BM[b000 + o[k]]);
+    const float2 c00 = __ldg(&BP[b000]), c01 = __ldg(&BP[b000 + sy]);
+    const float2 c10 = __ldg(&BP[b000 + sz]), c11 = __ldg(&BP[b000 + sz + sy]);
+    const unsigned bits = __ldg(&C8[b000]);
     // intensity: lerps along x, y, z, exact at t = 0 and t = 1 so that
     // quarter turns reproduce the voxels bit for bit
-    float v00 = lerp_exact(c[0].x, c[1].x, ax.t), v01 = lerp_exact(c[2].x, c[3].x, ax.t);
-    float v10 = lerp_exact(c[4].x, c[5].x, ax.t), v11 = lerp_exact(c[6].x, c[7].x, ax.t);
-    float v0 = lerp_exact(v00, v01, ay.t), v1 = lerp_exact(v10, v11, ay.t);
+    const float v00 = lerp_exact(c00.x, c00.y, ax.t), v01 = lerp_exact(c01.x, c01.y, ax.t);
+    const float v10 = lerp_exact(c10.x, c10.y, ax.t), v11 = lerp_exact(c11.x, c11.y, ax.t);
+    const float v0 = lerp_exact(v00, v01, ay.t), v1 = lerp_exact(v10, v11, ay.t);
     val = lerp_exact(v0, v1, az.t);
-    // mask decision: same lerp order, round-to-nearest, no contraction; when
-    // the eight corners agree every lerp returns their value exactly
-    const float msum = ((c[0].y + c[1].y) + (c[2].y + c[3].y)) + ((c[4].y + c[5].y) + (c[6].y + c[7].y));
-    if (msum == 0.0f || msum == 8.0f) {
-      m = msum == 8.0f ? 1 : 0;
-    } else {
-      float m00 = lerp_rn(c[0].y, c[1].y, ax.t), m01 = lerp_rn(c[2].y, c[3].y, ax.t);
-      float m10 = lerp_rn(c[4].y, c[5].y, ax.t), m11 = lerp_rn(c[6].y, c[7].y, ax.t);
-      float m0 = lerp_rn(m00, m01, ay.t), m1 = lerp_rn(m10, m11, ay.t);
-      float mm = lerp_rn(m0, m1, az.t);
-      m = (mm >= 0.5f) ? 1 : 0;
-    }
+    m = mask_decision(bits, ax.t, ay.t, az.t);
   }
 }
 
@@ -130,10 +134,10 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BM, co
 // (block: 8 x 4 x 4*RZ voxels).  Mask counts per axis (the slab bound's
 // marginals) are reduced with warp shuffles before one atomic per slot.
 // Grid: (x tiles, y tiles, z tiles * rotations).
-// MONLY: only the rotated mask, from M_B bytes, counted (no volumes written)
+// MONLY: only the rotated mask, counted (no volumes written)
 template <bool MONLY>
-__device__ __forceinline__ void resample_block(const float2* __restrict__ BM,
-                                               const uint8_t* __restrict__ MB,
+__device__ __forceinline__ void resample_block(const float2* __restrict__ BP,
+                                               const uint8_t* __restrict__ C8,
                                                const RotMat* __restrict__ rot, const Geo& g,
                                                float* __restrict__ Bh, uint8_t* __restrict__ Mh,
                                                int* __restrict__ msum, int* __restrict__ marg) {
@@ -153,11 +157,11 @@ __device__ __forceinline__ void resample_block(const float2* __restrict__ BM,
     int mk = 0;
     if (x < g.nx && y < g.ny && z < g.nz) {
       if constexpr (MONLY) {
-        mk = mask_voxel(MB, R, g, x, y, z);
+        mk = mask_voxel(C8, R, g, x, y, z);
       } else {
         float val;
         uint8_t m;
-        resample_voxel(BM, R, g, x, y, z, val, m);
+        resample_voxel(BP, C8, R, g, x, y, z, val, m);
         const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
         Bh[idx] = val;
         Mh[idx] = m;
@@ -203,16 +207,16 @@ __device__ __forceinline__ void resample_block(const float2* __restrict__ BM,
 }
 
 __global__ void __launch_bounds__(128)
-k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
-           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
-           int* __restrict__ marg) {
-  resample_block<false>(BM, nullptr, rot, g, Bh, Mh, msum, marg);
+k_resample(const float2* __restrict__ BP, const uint8_t* __restrict__ C8,
+           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh, uint8_t* __restrict__ Mh,
+           int* __restrict__ msum, int* __restrict__ marg) {
+  resample_block<false>(BP, C8, rot, g, Bh, Mh, msum, marg);
 }
 
 __global__ void __launch_bounds__(128)
-k_mask_counts(const uint8_t* __restrict__ MB, const RotMat* __restrict__ rot, Geo g,
+k_mask_counts(const uint8_t* __restrict__ C8, const RotMat* __restrict__ rot, Geo g,
               int* __restrict__ msum, int* __restrict__ marg) {
-  resample_block<true>(nullptr, MB, rot, g, nullptr, nullptr, msum, marg);
+  resample_block<true>(nullptr, C8, rot, g, nullptr, nullptr, msum, marg);
 }
 
 __global__ void k_marginals(const uint8_t* __restrict__ M, Geo g, int* __restrict__ marg) {

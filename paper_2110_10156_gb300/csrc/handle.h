@@ -49,7 +49,8 @@ struct cs_ngf_fixed {
   float2* UV = nullptr;
   float* Bh = nullptr;
   uint8_t* Mh = nullptr;
-  float2* BM = nullptr;        // (B, mask) pairs of the current call
+  float2* BP = nullptr;        // x-pairs (B[i], B[i+1]) of the current call
+  uint8_t* C8 = nullptr;       // corner codes of M_B of the current call
   float2* F02 = nullptr;
   float2* F13 = nullptr;
   int* msum = nullptr;
@@ -91,16 +92,16 @@ namespace detail {
 cs_ngf_status fail(cs_ngf_status s, const std::string& msg);
 // host FP64 quaternions -> FP32 matrices in f->rot_d[0..R)
 cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* quats, int R, cudaStream_t st);
-// (B, M_B) -> f->BM for the following score calls
+// (B, M_B) -> f->BP, f->C8 for the following score calls
 cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st);
 // Bound-limited padding (pad_mode CS_NGF_PAD_BOUND): the R uploaded
-// rotations of the floating mask MB (device) grouped into classes by the FFT
-// lengths their admitted shifts need.  Synchronises `st`.  perm[i] is the
+// rotations of the floating volume packed by pack_floating, grouped into
+// classes by the FFT lengths their admitted shifts need.  Synchronises `st`.  perm[i] is the
 // original index of the i-th rotation in class order (empty: order
 // unchanged; otherwise the device matrices are re-uploaded in that order);
 // class c covers [ends[c-1], ends[c]) and uses lengths pads[3c..3c+2].  In
 // other modes: one class with the lengths in use.
-cs_ngf_status plan_classes(cs_ngf_fixed* f, const uint8_t* MB, int R, cudaStream_t st,
+cs_ngf_status plan_classes(cs_ngf_fixed* f, int R, cudaStream_t st,
                            std::vector<int>& perm, std::vector<int>& ends, std::vector<int>& pads);
 // switch the handle to FFT lengths pad (recomputing the fixed spectra if they
 // change; synchronises `st` then)

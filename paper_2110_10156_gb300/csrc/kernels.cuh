@@ -110,16 +110,17 @@ __device__ __forceinline__ unsigned long long make_key(float s, unsigned lin) {
 // [trilinear M_B >= 0.5] inside [0, n-1]^3 (+-1e-4).  The sample point and the
 // mask decision use round-to-nearest FP32 operations in a fixed order (no
 // contraction), so the decision is reproducible bit for bit.  B and M_B are
-// read as (value, mask) pairs prepared by k_pack_bm.
-__global__ void k_pack_bm(const float* __restrict__ B, const uint8_t* __restrict__ MB, long long n,
-                          float2* __restrict__ BM);
-__global__ void k_resample(const float2* __restrict__ BM, const RotMat* __restrict__ rot, Geo g,
-                           float* __restrict__ Bh, uint8_t* __restrict__ Mh, int* __restrict__ msum,
-                           int* __restrict__ marg);
+// read as the x-pairs and corner codes k_pack_floating prepares (BP, C8: nvox
+// entries each).
+__global__ void k_pack_floating(const float* __restrict__ B, const uint8_t* __restrict__ MB, Geo g,
+                                float2* __restrict__ BP, uint8_t* __restrict__ C8);
+__global__ void k_resample(const float2* __restrict__ BP, const uint8_t* __restrict__ C8,
+                           const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
+                           uint8_t* __restrict__ Mh, int* __restrict__ msum, int* __restrict__ marg);
 // The rotated masks alone, counted into msum and marg as k_resample counts
-// them (same decisions, read from the 0/1 bytes of M_B, no volumes written):
+// them (the same decisions from the same corner codes, no volumes written):
 // the pre-pass that bounds the shifts of a whole call.  Grid: resample_grid.
-__global__ void k_mask_counts(const uint8_t* __restrict__ MB, const RotMat* __restrict__ rot, Geo g,
+__global__ void k_mask_counts(const uint8_t* __restrict__ C8, const RotMat* __restrict__ rot, Geo g,
                               int* __restrict__ msum, int* __restrict__ marg);
 constexpr int kResampleZGroups = 4;            // z-plane groups of 4 per resample block
 inline dim3 resample_grid(const Geo& g, int nrot) {

@@ -198,7 +198,7 @@ cs_ngf_status setup_job(cs_ngf_server* sv, Job* j, Slot* slot, bool fresh) {
   if (cs_ngf_status s = csngf::detail::upload_rotations(slot->f, j->quats.data(), j->R, st)) return s;
   if (cs_ngf_status s = csngf::detail::pack_floating(slot->f, slot->dB, slot->dMB, st)) return s;
   // FFT lengths per class of rotations (bound-limited padding), first class set up
-  if (cs_ngf_status s = csngf::detail::plan_classes(slot->f, slot->dMB, j->R, st, j->perm, j->class_end,
+  if (cs_ngf_status s = csngf::detail::plan_classes(slot->f, j->R, st, j->perm, j->class_end,
                                                     j->class_pad))
     return s;
   j->cls = 0;
