@@ -77,10 +77,16 @@ struct FwdXCfg {
   static constexpr int NI = FwdIn<FourStep<P, true, V>, HALF>::NI;
   static constexpr size_t ex_bytes = ((size_t)ROWS * FourStep<P, true, V>::CS * sizeof(float2) + 15) / 16 * 16;
   static constexpr size_t smem_bytes = ex_bytes + (HALF ? 0 : (size_t)NI * NT * sizeof(float4));
+  // three blocks per SM (at most 80 registers per thread): the gradient
+  // gathers and the per-field barriers leave the pass latency-bound, and the
+  // extra resident warps hide more of it than the few spilled registers cost
+  // (measured: 200-point lengths 2.13 -> 1.67 ms per 32 rotations, 320-point
+  // half-input lengths 72 -> 65 ms per 1000 rotations; 400 and 320 unchanged)
+  static constexpr int MIN_BLOCKS = 3;
 };
 
 template <int P, int ROWS, int ST, bool HALF, int V>
-__global__ void __launch_bounds__(ROWS * SplitV<P, V>::N2, 2)
+__global__ void __launch_bounds__(ROWS * SplitV<P, V>::N2, FwdXCfg<P, HALF, V>::MIN_BLOCKS)
 k_fwd_x(const float* __restrict__ Bh, const uint8_t* __restrict__ Mh, void* __restrict__ F0,
         const float2* __restrict__ tw, Geo g, long long nrows) {
   using FS = FourStep<P, true, V>;
