@@ -51,3 +51,33 @@ def check_maps(oracle_map, gpu_map, tau=TAU_FP32):
         assert err <= tau * scale, (err, scale)
         return err / scale
     return 0.0
+
+
+def face_neighbours(chi):
+    """chi and its six face neighbours (the shifts a sampled check evaluates)."""
+    out = [tuple(int(c) for c in chi)]
+    for a in range(3):
+        for d in (-1, 1):
+            c = list(out[0])
+            c[a] += d
+            out.append(tuple(c))
+    return out
+
+
+def check_best_at_sampled_shifts(oracle_map, gpu_score, gpu_shift, tau=TAU_FP32):
+    """Sampled form of the gap rule for volumes whose full oracle map is too
+    large: the oracle's direct sum at the GPU's shift must be valid and within
+    tau of the GPU's score (scores lie in [0, 1]), and no valid face
+    neighbour may beat it by more than tau (the GPU's shift is a local
+    maximum of the oracle's map)."""
+    dims = tuple((s + 1) // 2 for s in oracle_map.shape)
+    at = lambda chi: float(oracle_map[tuple(int(c) + n - 1 for c, n in zip(chi, dims))])
+    chis = face_neighbours(gpu_shift)
+    o_at_gpu = at(chis[0])
+    assert np.isfinite(o_at_gpu), f"GPU shift {gpu_shift} is not valid for the oracle"
+    assert abs(float(gpu_score) - o_at_gpu) <= tau, (gpu_score, o_at_gpu)
+    for chi in chis[1:]:
+        if all(abs(c) <= n - 1 for c, n in zip(chi, dims)):
+            v = at(chi)
+            if np.isfinite(v):
+                assert v <= o_at_gpu + tau, (chi, v, gpu_shift, o_at_gpu)

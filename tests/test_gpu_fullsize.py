@@ -1,4 +1,5 @@
-"""Full-size parity: the 150^3 / 320^3 workload with 1000 rotations, scored in
+"""Full-size parity: the 150^3 workload with 1000 rotations and the 256^3
+workload with 5000 rotations, scored in
 the same launch configuration the bench times (automatic batch), checked
 against the FP64 oracle on sampled rotations and by properties on all."""
 import numpy as np
@@ -6,7 +7,7 @@ import pytest
 
 from oracle import cs_ngf_oracle as O
 from paper_2110_10156_gb300 import synth
-from tests.parity_util import check_best_against_map
+from tests.parity_util import check_best_against_map, check_best_at_sampled_shifts, face_neighbours
 
 pytestmark = pytest.mark.gpu
 
@@ -69,3 +70,46 @@ def test_150_cubed_1000_rotations(cs, pair150, oracle150, precision, tau, pad_mo
     for r, omap in oracle150.items():
         check_best_against_map(omap, sc[r], sh[r], tau=tau)
     f.release()
+
+
+@pytest.fixture(scope="module")
+def pair256():
+    return synth.config_pair(4)
+
+
+def test_256_cubed_5000_rotations_fp32_and_fp16(cs, pair256):
+    """The 256^3 pair with 5000 rotations in the bench's launch configuration
+    (memory-sized batch), in FP32 and in the FP16 form.  All rotations are
+    checked by properties; the true and one sampled rotation by the oracle's
+    direct sum (Eq. 5) at the GPU's shift and its face neighbours."""
+    p = pair256
+    R = len(p.quats)
+    assert R == 5000
+    B, MB = dev(p.B), dev(p.MB)
+    res = {}
+    for precision in ("fp32", "fp16"):
+        f = cs.prepare_fixed(dev(p.A), dev(p.MA), precision=precision)
+        sc, sh = [t.cpu().numpy() for t in f.score_rotations(B, MB, p.quats)]
+        assert f.max_pad == (512, 512, 512)
+        f.release()
+        assert sc.shape == (R,) and sh.shape == (R, 3)
+        fin = np.isfinite(sc)
+        assert fin.all()
+        assert sc.min() >= -1e-6 and sc.max() <= 1 + 1e-6
+        assert np.all(np.abs(sh) <= 255)
+        assert int(np.argmax(sc)) == p.true_index
+        assert tuple(sh[p.true_index]) == p.t_zyx
+        res[precision] = (sc, sh)
+    # FP16 against FP32: the same global argmax, scores within the form's tolerance
+    assert float(np.max(np.abs(res["fp16"][0] - res["fp32"][0]))) <= 1e-2
+    rng = np.random.default_rng(256)
+    sample = [p.true_index] + [int(i) for i in rng.choice(R, 1, replace=False)]
+    for r in sample:
+        Bh, Mh = O.resample(p.B, p.MB, p.quats[r])
+        chis = set()
+        for precision in res:
+            chis.update(face_neighbours(res[precision][1][r]))
+        chis = [c for c in chis if all(abs(v) <= 255 for v in c)]
+        omap, _ = O.csngf_direct(p.A, p.MA, Bh, Mh, 1e-5, 0.5, chis=chis)
+        check_best_at_sampled_shifts(omap, res["fp32"][0][r], res["fp32"][1][r], tau=1e-4)
+        check_best_at_sampled_shifts(omap, res["fp16"][0][r], res["fp16"][1][r], tau=1e-2)
