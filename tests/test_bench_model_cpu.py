@@ -1,0 +1,99 @@
+"""The bench's roofline numerators and the ncu-summary parser, on the CPU.
+
+The byte model is checked against the buffer sizes of the HBM layout written
+out field by field; the flop model against 5 L log2 L per transform counted
+column by column; the parser against a small ncu CSV whose sums are known."""
+import importlib.util
+import json
+import math
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_byte_model_at_the_headline_lengths(bench):
+    dims, pad, nb = (150, 150, 150), (200, 200, 200), 32
+    nvox = 150 ** 3
+    # per rotation: three packed channel fields of 8 B plus half a mask field of 8 B
+    field_bytes = 3 * 8 + 8 / 2
+    F0 = field_bytes * 150 * 150 * 200          # [z][y][kx] after the x transform
+    F1 = field_bytes * 150 * 200 * 200          # [kx][z][ky] after the y transform
+    per = lambda st: bench.stage_bytes(dims, pad, nb, st) / nb
+    assert per("resample") == nvox * 5          # B-hat (4 B) and M-hat (1 B) written
+    assert per("fwd_x") == pytest.approx(nvox * 5 + F0)
+    assert per("fwd_y") == pytest.approx(F0 + F1)
+    UV = 7 * 101 * 200 * 200 * 8                 # fixed spectra, loaded once per launch
+    assert per("zmac") == pytest.approx(F1 + UV / nb)
+    F2, F3 = 299 * 200 * 200 * 8, 299 * 299 * 200 * 8
+    assert per("inv_y") == F2 + F3 and per("inv_x") == F3
+    # the figures the design notes quote (MB per rotation)
+    assert round(per("fwd_x") / 1e6) == 143 and round(per("fwd_y") / 1e6) == 294
+    assert round(per("zmac") / 1e6) == 175
+
+
+def test_byte_model_halves_channel_bytes_in_16_bit_forms(bench):
+    dims, pad = (150, 150, 150), (200, 200, 200)
+    f32 = bench.stage_bytes(dims, pad, 2, "fwd_y")
+    b16 = bench.stage_bytes(dims, pad, 2, "fwd_y", precision="bf16")
+    E = 150 * 150 * 200 + 150 * 200 * 200      # F0 + F1 element positions
+    assert f32 - b16 == 2 * 3 * 4 * E           # 2 rotations x 3 channel fields x 4 B saved
+
+
+def test_flop_model_counts_transforms_and_products(bench):
+    dims, pad, nb = (150, 150, 150), (200, 200, 200), 2
+    L, cols = 200, 200 * 200
+    fwd = 5 * L * math.log2(L)                  # 150 > 100: no zero half to prune
+    fields = 3 * nb + 1
+    mac = 101 * 200 * 200 * (16 * 3 + 20) * nb
+    want = fields * cols * fwd + nb * cols * 5 * L * math.log2(L) + mac
+    assert bench.zmac_flops(dims, pad, nb) == pytest.approx(want)
+    # full padding: the input is zero past L/2, so the first radix-2 stage is
+    # pruned; a pair of rotations shares one mask field (3.5 fields each)
+    L = 320
+    got = bench.zmac_flops(dims, (L, L, L), 2) / 2
+    fwd = 5 * L * (math.log2(L) - 1) + L
+    want = 3.5 * L * L * fwd + L * L * 5 * L * math.log2(L) + 161 * L * L * 68
+    assert got == pytest.approx(want)
+    assert round(got / 1e9, 1) == 6.8
+    assert round(bench.zmac_flops(dims, pad, 2) / 2 / 1e9, 1) == 1.6
+
+
+def _csv_row(i, name, metric, unit, value):
+    return f'"{i}","1","python","127.0.0.1","{name}","1","7","(1,1,1)","(1,1,1)","0","10.3",' \
+           f'"Section","{metric}","{unit}","{value}"\n'
+
+
+def test_traffic_summary_parser(tmp_path, bench):
+    from paper_2110_10156_gb300 import profile_workload as pw
+    head = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",' \
+           '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit",' \
+           '"Metric Value"\n'
+    rows = [
+        _csv_row(0, "void csngf::k_fwd_x<200, 10, 0, 0, 1>(const float *)", "dram__bytes_read.sum", "Mbyte", "999"),
+        _csv_row(1, "csngf::k_resample(const float2 *)", "dram__bytes_read.sum", "Mbyte", "1.5"),
+        _csv_row(1, "csngf::k_resample(const float2 *)", "dram__bytes_write.sum", "Mbyte", "2.5"),
+        _csv_row(2, "void csngf::k_zmac<200, 0, 0, 0>(const void *)", "dram__bytes_read.sum", "Gbyte", "1.25"),
+        _csv_row(2, "void csngf::k_zmac<200, 0, 0, 0>(const void *)", "dram__bytes_write.sum", "byte", "1,000"),
+        _csv_row(2, "void csngf::k_zmac<200, 0, 0, 0>(const void *)", "gpu__time_duration.sum", "ms", "3"),
+    ]
+    csv_path = tmp_path / "traffic.csv"
+    csv_path.write_text("==PROF== preamble\n" + head + "".join(rows))
+    out_path = tmp_path / "traffic.json"
+    out = pw.traffic_from_csv(str(csv_path), 2, str(out_path))
+    assert out["src_hash"] == bench.kernel_source_hash()
+    st = out["stages"]
+    # the fixed volume's pass before the first resample is left out
+    assert set(st) == {"resample", "zmac"}
+    assert st["resample"] == {"launches": 1, "dram_bytes_per_rotation": 2.0e6}
+    assert st["zmac"]["dram_bytes_per_rotation"] == pytest.approx((1.25e9 + 1000) / 2)
+    assert json.loads(out_path.read_text()) == out
