@@ -65,7 +65,7 @@ def test_flop_model_counts_transforms_and_products(bench):
     want = 3.5 * L * L * fwd + L * L * 5 * L * math.log2(L) + 161 * L * L * 68
     assert got == pytest.approx(want)
     assert round(got / 1e9, 1) == 6.8
-    assert round(bench.zmac_flops(dims, pad, 2) / 2 / 1e9, 1) == 1.6
+    assert round(bench.zmac_flops(dims, pad, 2) / 2 / 1e9, 2) == 1.65
 
 
 def _csv_row(i, name, metric, unit, value):
