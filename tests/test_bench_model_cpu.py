@@ -7,6 +7,7 @@ import importlib.util
 import json
 import math
 import os
+import sys
 
 import pytest
 
@@ -15,8 +16,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def bench():
+    # registered under its own name so that its pool workers (spawn) can
+    # import it and unpickle its functions
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
     spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
     mod = importlib.util.module_from_spec(spec)
+    sys.modules["bench"] = mod
     spec.loader.exec_module(mod)
     return mod
 
@@ -97,3 +103,49 @@ def test_traffic_summary_parser(tmp_path, bench):
     assert st["resample"] == {"launches": 1, "dram_bytes_per_rotation": 2.0e6}
     assert st["zmac"]["dram_bytes_per_rotation"] == pytest.approx((1.25e9 + 1000) / 2)
     assert json.loads(out_path.read_text()) == out
+
+
+def test_compare_with_oracle(bench):
+    inf = float("inf")
+    gpu_s = [0.5, 0.25, -inf, 0.7, -inf]
+    gpu_c = [(1, 2, 3), (0, 0, 1), (0, 0, 0), (4, 4, 4), (0, 0, 0)]
+    oracle = [(0.5 + 2e-7, (1, 2, 3)), (0.25, (0, 1, 0)), (-inf, (0, 0, 0)), (0.7, (4, 4, 4)),
+              (0.1, (1, 1, 1))]
+    out = bench.compare_with_oracle(gpu_s, gpu_c, oracle)
+    assert out["rotations"] == 5
+    assert out["max_abs_score_err"] == pytest.approx(2e-7)
+    assert out["same_shift"] == 3                 # rotations 0, 2 (both invalid) and 3
+    assert out["validity_mismatch"] == 1          # rotation 4
+
+
+def test_reference_arm_prints_one_line(bench, monkeypatch, capsys):
+    """The reference arm's JSON line, with the oracle timing stubbed out (the
+    real arm runs the FP64 oracle for minutes)."""
+    import argparse
+    import numpy as np
+    monkeypatch.setattr(bench, "load_pair", lambda config, n: {"quats": np.zeros((n, 4))})
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda pair, n, cores: (n / 2.0, 2.0, [(0.5, (0, 0, 0))] * n))
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    args = argparse.Namespace(config=1, rotations=1000, ref_sample=4, warmup=3, steps=2)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["higher_is_better"] is True
+    assert line["value"] == pytest.approx(2.0)      # 4 rotations per 2 s step
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_oracle_sample_returns_the_oracles_best(bench):
+    """The CPU leg's pool returns each sampled rotation's best (score, shift),
+    the values compare_with_oracle checks the GPU's results against."""
+    from oracle import cs_ngf_oracle as O
+    from paper_2110_10156_gb300 import synth
+    p = synth.small_pair(77, (10, 9, 11), n_rot=3, masks="full")
+    pair = {"A": p.A, "MA": p.MA, "B": p.B, "MB": p.MB, "quats": p.quats}
+    rate, dt, best = bench.oracle_sample(pair, 2, 2)
+    assert rate > 0 and dt > 0 and len(best) == 2
+    for q, (s, chi) in zip(p.quats[:2], best):
+        want = O.best_of_map(O.score_map(p.A, p.MA, p.B, p.MB, q)[0])
+        assert s == want[0] and tuple(chi) == tuple(want[1])
