@@ -418,23 +418,6 @@ typedef struct {
 int32_t cs_ngf_tuning(int32_t cap, cs_ngf_tuning_entry* out);
 void cs_ngf_tuning_reset(void);
 
-/* Persistent autotuning cache, so that a later process at the same lengths
- * skips the timing runs.  cs_ngf_tuning_save writes this process's choices to
- * the text file path (host string; one line per entry: pass, length,
- * half_input, storage, variant, ms[0], ms[1]; '#' lines are comments) and
- * replaces the file.  cs_ngf_tuning_load reads such a file and merges its
- * entries into the process's choices (an entry for a key already chosen
- * replaces it); handles with autotune = 1 then use them instead of timing.
- * Every split computes the same scores, so a loaded choice changes timing
- * only.  An entry is accepted only for a pass in 0..4 and a supported length
- * that has two splits, with half_input and storage in range (both 0 for the
- * inverse passes) and variant 0 or 1.  Errors: EINVAL for a NULL path, a file
- * that cannot be opened, read or written, or any malformed or out-of-range
- * line (the detail names the line; nothing is merged then).  Host only: no
- * device work. */
-cs_ngf_status cs_ngf_tuning_save(const char* path);
-cs_ngf_status cs_ngf_tuning_load(const char* path);
-
 /* The length classes bound-limited padding forms, computed on the host
  * alone (what a scoring call does after counting the rotated masks):
  *   dims     {nz, ny, nx}; max_pad the largest lengths (each >= 2n - 1)

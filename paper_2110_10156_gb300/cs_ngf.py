@@ -32,8 +32,7 @@ EXPORTED = (
     "cs_ngf_server_default_config", "cs_ngf_server_create", "cs_ngf_server_submit",
     "cs_ngf_server_cancel", "cs_ngf_server_wait", "cs_ngf_server_stats", "cs_ngf_server_destroy",
     "cs_ngf_search_default_config", "cs_ngf_global_align", "cs_ngf_length_sets",
-    "cs_ngf_tuning", "cs_ngf_tuning_reset", "cs_ngf_plan_lengths", "cs_ngf_tuning_save",
-    "cs_ngf_tuning_load",
+    "cs_ngf_tuning", "cs_ngf_tuning_reset", "cs_ngf_plan_lengths",
 )
 
 MAX_LEVELS = 8
@@ -124,10 +123,6 @@ _lib.cs_ngf_tuning.argtypes = [_i32, ctypes.c_void_p]
 _lib.cs_ngf_tuning.restype = _i32
 _lib.cs_ngf_tuning_reset.argtypes = []
 _lib.cs_ngf_tuning_reset.restype = None
-_lib.cs_ngf_tuning_save.argtypes = [ctypes.c_char_p]
-_lib.cs_ngf_tuning_save.restype = _i32
-_lib.cs_ngf_tuning_load.argtypes = [ctypes.c_char_p]
-_lib.cs_ngf_tuning_load.restype = _i32
 _lib.cs_ngf_length_sets.argtypes = [ctypes.c_void_p, _i32, ctypes.c_void_p, ctypes.c_void_p]
 _lib.cs_ngf_length_sets.restype = _i32
 _lib.cs_ngf_auto_pad.argtypes = [_i32]
@@ -220,17 +215,6 @@ def tuning():
 
 def tuning_reset():
     _lib.cs_ngf_tuning_reset()
-
-
-def tuning_save(path):
-    """Write the process's autotuning choices to a text file (cs_ngf_tuning_save)."""
-    _check(_lib.cs_ngf_tuning_save(os.fsencode(path)), "cs_ngf_tuning_save")
-
-
-def tuning_load(path):
-    """Merge autotuning choices from a file written by tuning_save
-    (cs_ngf_tuning_load); handles with autotune=True then skip timing them."""
-    _check(_lib.cs_ngf_tuning_load(os.fsencode(path)), "cs_ngf_tuning_load")
 
 
 def auto_pad(n: int) -> int:

@@ -1192,69 +1192,6 @@ void cs_ngf_tuning_reset(void) {
   g_tune.clear();
 }
 
-cs_ngf_status cs_ngf_tuning_save(const char* path) {
-  g_last_error.clear();
-  if (!path) return fail(CS_NGF_EINVAL, "path is NULL");
-  std::vector<std::pair<TuneKey, TuneVal>> entries;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    entries.assign(g_tune.begin(), g_tune.end());
-  }
-  FILE* fh = std::fopen(path, "w");
-  if (!fh) return fail(CS_NGF_EINVAL, std::string("cannot open ") + path + " for writing");
-  bool ok = std::fprintf(fh, "# cs_ngf tuning: pass length half_input storage variant ms0 ms1\n") > 0;
-  for (const auto& kv : entries)
-    ok = ok && std::fprintf(fh, "%d %d %d %d %d %.6g %.6g\n", kv.first.pass, kv.first.P, kv.first.half,
-                            kv.first.store, kv.second.variant, (double)kv.second.ms[0],
-                            (double)kv.second.ms[1]) > 0;
-  ok = (std::fclose(fh) == 0) && ok;
-  if (!ok) return fail(CS_NGF_EINVAL, std::string("cannot write ") + path);
-  return CS_NGF_OK;
-}
-
-cs_ngf_status cs_ngf_tuning_load(const char* path) {
-  g_last_error.clear();
-  if (!path) return fail(CS_NGF_EINVAL, "path is NULL");
-  FILE* fh = std::fopen(path, "r");
-  if (!fh) return fail(CS_NGF_EINVAL, std::string("cannot open ") + path);
-  std::vector<std::pair<TuneKey, TuneVal>> entries;
-  char buf[512];
-  int line = 0;
-  std::string err;
-  while (err.empty() && std::fgets(buf, sizeof buf, fh)) {
-    ++line;
-    const size_t len = std::strlen(buf);
-    if (len + 1 == sizeof buf && buf[len - 1] != '\n') { err = "line too long"; break; }
-    const char* p = buf;
-    while (*p == ' ' || *p == '\t') ++p;
-    if (*p == '#' || *p == '\n' || *p == '\r' || *p == '\0') continue;
-    int pass, P, half, store, variant, used = 0;
-    float ms0, ms1;
-    if (std::sscanf(p, "%d %d %d %d %d %f %f %n", &pass, &P, &half, &store, &variant, &ms0, &ms1,
-                    &used) != 7 || p[used] != '\0') {
-      err = "expected 5 integers and 2 times";
-      break;
-    }
-    const bool inverse = pass == 3 || pass == 4;
-    if (pass < 0 || pass >= kPasses) err = "pass out of range";
-    else if (!pad_supported(P) || !has_alt_split(P)) err = "length has no alternative split";
-    else if (half < 0 || half > 1 || (inverse && half != 0)) err = "half_input out of range";
-    else if (store < 0 || store > 2 || (inverse && store != 0)) err = "storage out of range";
-    else if (variant < 0 || variant > 1) err = "variant out of range";
-    else if (!(ms0 >= 0.0f) || !(ms1 >= 0.0f) || !std::isfinite(ms0) || !std::isfinite(ms1))
-      err = "times must be finite and non-negative";
-    else entries.push_back({{pass, P, half, store}, {variant, {ms0, ms1}}});
-  }
-  const bool read_error = std::ferror(fh) != 0;
-  std::fclose(fh);
-  if (!err.empty())
-    return fail(CS_NGF_EINVAL, std::string(path) + " line " + std::to_string(line) + ": " + err);
-  if (read_error) return fail(CS_NGF_EINVAL, std::string("cannot read ") + path);
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  for (const auto& kv : entries) g_tune[kv.first] = kv.second;
-  return CS_NGF_OK;
-}
-
 int32_t cs_ngf_length_sets(const cs_ngf_fixed* f, int32_t cap, int32_t* pads, int32_t* counts) {
   if (!f) return 0;
   const int n = (int)f->last_counts.size();

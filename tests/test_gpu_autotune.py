@@ -108,32 +108,3 @@ def test_alternative_splits_with_full_length_inputs(cs):
     for r, q in enumerate(p.quats):
         omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q)
         check_best_against_map(omap, sc[r], sh[r])
-
-
-def test_saved_choices_are_used_without_timing(cs, tmp_path):
-    """A cache written by tuning_save and read back into an empty table: an
-    autotuned handle then times nothing and scores bit for bit as the handle
-    that made the choices."""
-    cs.tuning_reset()
-    p = synth.small_pair(43, (36, 30, 34), masks="threshold", n_rot=6)
-    kw = dict(batch=4, pad_mode="full", autotune=True)                # lengths 80, 64, 80
-    f = cs.prepare_fixed(dev(p.A), dev(p.MA), **kw)
-    sc, sh = [t.cpu().numpy() for t in f.score_rotations(dev(p.B), dev(p.MB), p.quats)]
-    table = cs.tuning()
-    assert len(table) == 5
-    path = tmp_path / "tuning.txt"
-    cs.tuning_save(path)
-    cs.tuning_reset()
-    cs.tuning_load(path)
-    g = cs.prepare_fixed(dev(p.A), dev(p.MA), **kw)
-    sg, cg = [t.cpu().numpy() for t in g.score_rotations(dev(p.B), dev(p.MB), p.quats)]
-    after = cs.tuning()
-    assert [(e["stage"], e["length"], e["variant"]) for e in after] == \
-           [(e["stage"], e["length"], e["variant"]) for e in table]
-    for a, b in zip(after, table):                 # the file's times, not new ones
-        assert a["ms"] == pytest.approx(b["ms"], rel=1e-5)
-    np.testing.assert_array_equal(sg, sc)
-    np.testing.assert_array_equal(cg, sh)
-    f.release()
-    g.release()
-    cs.tuning_reset()
