@@ -252,6 +252,8 @@ class Fixed:
         at new lengths) or "alternative" (the second split wherever a length
         has one)."""
         import torch
+        _dev_ptr(A, torch.float32, "A")
+        _dev_ptr(MA, torch.uint8, "maskA")
         if A.dim() != 3:
             raise ValueError("A must be [nz][ny][nx]")
         self.dims = tuple(int(d) for d in A.shape)
@@ -439,6 +441,9 @@ def score_rotations_noalloc(A, MA, B, MB, quats, eps=1e-5, gamma=0.5, out_score=
     must not overlap on the GPU.  The outputs are allocated here by torch
     unless given."""
     import torch
+    for t, dt, name in ((A, torch.float32, "A"), (MA, torch.uint8, "maskA"),
+                        (B, torch.float32, "B"), (MB, torch.uint8, "maskB")):
+        _dev_ptr(t, dt, name)
     dims = tuple(int(d) for d in A.shape)
     q = _quats(quats)
     R = q.shape[0]
