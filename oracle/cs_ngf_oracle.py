@@ -105,9 +105,24 @@ def sample_points_f32(R: np.ndarray, dims):
     return p
 
 
+# Section 3.2 reading of the rotated mask: sample points within this distance
+# outside [0, n-1] still count as inside the domain (they sample the face).
+DOMAIN_SLACK = 1e-4
+
+
+def _lerp(a, b, t):
+    """a + t (b - a) in FP32 (the order the mask decision is taken in)."""
+    return (a + t * (b - a)).astype(F32)
+
+
+def _mask_on(m):
+    """The rotated mask is set where the interpolated mask reaches one half."""
+    return m >= F32(0.5)
+
+
 def _axis_setup(p, n):
     """Domain test, clamped base index and fraction for one axis (FP32)."""
-    slack = F32(1e-4)
+    slack = F32(DOMAIN_SLACK)
     hi = F32(n - 1) + slack
     inside = (p >= -slack) & (p <= hi)
     pc = np.minimum(np.maximum(p, F32(0.0)), F32(n - 1))
@@ -145,18 +160,14 @@ def resample(B: np.ndarray, MB: np.ndarray, q):
 
     # mask decision in FP32: lerp along x, then y, then z; lerp(a,b,t)=a+t*(b-a)
     M = MB.astype(F32)
-
-    def lerp(a, b, t):
-        return (a + t * (b - a)).astype(F32)
-
-    m00 = lerp(M[z0, y0, x0], M[z0, y0, x1], tx)
-    m01 = lerp(M[z0, y1, x0], M[z0, y1, x1], tx)
-    m10 = lerp(M[z1, y0, x0], M[z1, y0, x1], tx)
-    m11 = lerp(M[z1, y1, x0], M[z1, y1, x1], tx)
-    m0 = lerp(m00, m01, ty)
-    m1 = lerp(m10, m11, ty)
-    m = lerp(m0, m1, tz)
-    Mhat = (inside & (m >= F32(0.5))).astype(np.uint8)
+    m00 = _lerp(M[z0, y0, x0], M[z0, y0, x1], tx)
+    m01 = _lerp(M[z0, y1, x0], M[z0, y1, x1], tx)
+    m10 = _lerp(M[z1, y0, x0], M[z1, y0, x1], tx)
+    m11 = _lerp(M[z1, y1, x0], M[z1, y1, x1], tx)
+    m0 = _lerp(m00, m01, ty)
+    m1 = _lerp(m10, m11, ty)
+    m = _lerp(m0, m1, tz)
+    Mhat = (inside & _mask_on(m)).astype(np.uint8)
     return Bhat, Mhat
 
 

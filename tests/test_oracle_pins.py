@@ -310,6 +310,162 @@ def test_generator_pair_recovers_truth_small():
     assert chi == p.t_zyx
 
 
+# ------------------------------------- rotated mask at fractional weights
+def scalar_resample(B, MB, R, slack=1e-4):
+    """B_hat and M_hat voxel by voxel from the Section 3.2 reading, written
+    independently of the oracle: the sample point p = R (x - c) + c (FP32,
+    in the order the reading fixes), the domain test against [0, n-1] with
+    the slack, then trilinear interpolation in its hat-function form,
+    f(p) = sum_k f[k] prod_i max(0, 1 - |p_i - k_i|) over the grid (FP64, at
+    p clamped onto the box), with no base index or cell logic.  Returns the
+    intensities, the interpolated mask m (FP64) and the domain flags."""
+    nz, ny, nx = B.shape
+    n = (nx, ny, nz)
+    f32 = np.float32
+    Rf = R.astype(f32)
+    c = [f32((v - 1) / 2) for v in n]
+    val = np.zeros(B.shape)
+    mval = np.zeros(B.shape)
+    inside = np.zeros(B.shape, dtype=bool)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                d = (f32(x) - c[0], f32(y) - c[1], f32(z) - c[2])
+                p = []
+                for i in range(3):
+                    acc = f32(Rf[i, 0] * d[0])
+                    acc = f32(acc + f32(Rf[i, 1] * d[1]))
+                    acc = f32(acc + f32(Rf[i, 2] * d[2]))
+                    p.append(float(f32(acc + c[i])))
+                ok = all(-slack <= p[i] <= (n[i] - 1) + slack for i in range(3))
+                inside[z, y, x] = ok
+                pc = [min(max(p[i], 0.0), float(n[i] - 1)) for i in range(3)]
+                hats = [[(k, max(0.0, 1.0 - abs(pc[i] - k))) for k in range(n[i])] for i in range(3)]
+                hats = [[(k, w) for k, w in h if w > 0.0] for h in hats]
+                v = m = 0.0
+                for kz, wz in hats[2]:
+                    for ky, wy in hats[1]:
+                        for kx, wx in hats[0]:
+                            v += wz * wy * wx * float(B[kz, ky, kx])
+                            m += wz * wy * wx * float(MB[kz, ky, kx])
+                val[z, y, x] = v if ok else 0.0
+                mval[z, y, x] = m
+    return val, mval, inside
+
+
+def _check_resample_against_scalar(B, MB, q, require_exact_half=False):
+    """The oracle's resample against the scalar definition: intensities to
+    1e-12, and the mask decision [m >= 1/2] and domain test wherever the
+    FP32 lerps cannot round across the half (|m - 1/2| > 1e-6); where m is
+    exactly 1/2 the decision must be 'on'.  Returns (exact halves, skipped)."""
+    R = O.quat_to_rotmat(q)
+    Bh, Mh = O.resample(B, MB, q)
+    val, m, inside = scalar_resample(B, MB, R)
+    np.testing.assert_allclose(Bh, val, rtol=0, atol=1e-12)
+    want = inside & (m >= 0.5)
+    half = inside & (m == 0.5)
+    decided = ~inside | (np.abs(m - 0.5) > 1e-6) | half
+    assert np.array_equal(Mh.astype(bool)[decided], want[decided])
+    if require_exact_half:
+        assert decided.all()
+    return int(half.sum()), int((~decided).sum())
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_resample_matches_scalar_definition_general_rotations(seed):
+    """Non-axis rotations on tiny volumes: nearly every voxel has fractional
+    weights on all three axes and many sample points leave the domain."""
+    rng = np.random.default_rng(100 + seed)
+    dims = [(5, 6, 4), (6, 6, 6), (4, 5, 6)][seed]
+    B = rng.random(dims)
+    MB = (rng.random(dims) < 0.5).astype(np.uint8)
+    total_skipped = 0
+    for q in synth.random_quaternions(rng, 4):
+        _, skipped = _check_resample_against_scalar(B, MB, q)
+        total_skipped += skipped
+    assert total_skipped <= 2      # the check decides (almost) every voxel
+
+
+def test_resample_mask_exactly_half_is_on():
+    """A quarter turn about z on a 4 x 5 x 4 volume puts every sample point
+    half-way between voxels in x and y (c_x = 1.5, c_y = 2), so the
+    interpolated mask is the mean of four corners, exactly 1/2 wherever two
+    are set (all FP32 lerps exact): those voxels must be in the mask.  Rows
+    whose x sample lands at -0.5 or 3.5 fall outside the domain."""
+    rng = np.random.default_rng(7)
+    dims = (4, 5, 4)
+    B = rng.random(dims)
+    MB = (rng.random(dims) < 0.5).astype(np.uint8)
+    q = synth.axis_angle_quaternion([0, 0, 1], np.pi / 2)
+    halves, _ = _check_resample_against_scalar(B, MB, q, require_exact_half=True)
+    assert halves >= 5
+    R = O.quat_to_rotmat(q)
+    _, _, inside = scalar_resample(B, MB, R)
+    assert 0 < inside.sum() < inside.size
+
+
+def test_resample_domain_slack_and_face_clamp():
+    """A rotation of 7.5e-5 rad about z on a 5^3 volume moves the x sample
+    points of the faces x = 0 and x = 4 by up to 1.5e-4: points within the
+    1e-4 slack count as inside and sample the face itself; points beyond it
+    are outside (B_hat = 0, mask 0)."""
+    rng = np.random.default_rng(8)
+    dims = (5, 5, 5)
+    B = rng.random(dims) + 1.0
+    MB = np.ones(dims, dtype=np.uint8)
+    q = synth.axis_angle_quaternion([0, 0, 1], 7.5e-5)
+    _check_resample_against_scalar(B, MB, q, require_exact_half=True)
+    R = O.quat_to_rotmat(q)
+    px, _, _ = O.sample_points_f32(R, dims)
+    Bh, Mh = O.resample(B, MB, q)
+    slack_pts = ((px < 0) & (px >= -1e-4)) | ((px > 4) & (px <= 4 + 1e-4))
+    out_pts = (px < -1e-4) | (px > 4 + 1e-4)
+    assert slack_pts.sum() >= 10 and out_pts.sum() >= 10
+    assert np.all(Mh[slack_pts] == 1) and np.all(Mh[out_pts] == 0)
+    assert np.all(Bh[out_pts] == 0.0)
+    face = np.where(px[slack_pts] < 0, 0, 4)
+    zs, ys, _ = np.nonzero(slack_pts)
+    # at the slack points y is fractional, so compare with the face's own interpolation
+    val, _, _ = scalar_resample(B, MB, R)
+    np.testing.assert_allclose(Bh[slack_pts], val[slack_pts], rtol=0, atol=1e-12)
+    assert len(face) == len(zs)
+
+
+def test_best_of_map_tie_rule_by_scan():
+    """The argmax tie rule (largest score, then the smallest (z, y, x) shift)
+    against a plain lexicographic scan that keeps the first strictly larger
+    value, on maps with planted equal maxima, -inf holes and an empty map."""
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        dims = tuple(int(v) for v in rng.integers(2, 5, size=3))
+        shape = tuple(2 * n - 1 for n in dims)
+        m = np.round(rng.random(shape), 1)          # many exact ties
+        m[rng.random(shape) < 0.3] = -np.inf
+        if trial == 0:
+            m[:] = -np.inf
+        best, chi = None, (0, 0, 0)
+        for idx in itertools.product(*[range(s) for s in shape]):
+            if np.isfinite(m[idx]) and (best is None or m[idx] > best):
+                best, chi = float(m[idx]), tuple(i - (n - 1) for i, n in zip(idx, dims))
+        got = O.best_of_map(m)
+        if best is None:
+            assert got[0] == -np.inf and got[1] == (0, 0, 0)
+        else:
+            assert got == (best, chi)
+
+
+def test_align_tie_goes_to_smallest_rotation_index(monkeypatch):
+    """Fig. 1's maximum over rotations: equal best scores go to the smallest
+    rotation index (checked with a stand-in per-rotation scorer)."""
+    monkeypatch.setattr(O, "score_rotations",
+                        lambda *a, **k: (np.array([0.2, 0.7, 0.7, -np.inf]),
+                                         np.array([[0, 0, 0], [1, 2, 3], [4, 5, 6], [0, 0, 0]])))
+    assert O.align(None, None, None, None, [None] * 4) == (0.7, 1, (1, 2, 3))
+    monkeypatch.setattr(O, "score_rotations",
+                        lambda *a, **k: (np.full(3, -np.inf), np.zeros((3, 3), dtype=np.int64)))
+    assert O.align(None, None, None, None, [None] * 3) == (-np.inf, -1, (0, 0, 0))
+
+
 # ------------------------------------------------------------ mutations
 def _pins_pass():
     """The pins re-run as plain functions; True if all of them pass."""
@@ -321,11 +477,14 @@ def _pins_pass():
         lambda: test_quarter_turn_resample_is_exact_permutation(2),
         test_integer_shift_at_identity_recovers_shift_and_closed_form,
         test_gradient_and_ngf_on_linear_ramp,
+        lambda: test_resample_matches_scalar_definition_general_rotations(0),
+        test_resample_mask_exactly_half_is_on,
+        test_resample_domain_slack_and_face_clamp,
     ]
     try:
         for c in checks:
             c()
-    except AssertionError:
+    except (AssertionError, IndexError):
         return False
     return True
 
@@ -337,6 +496,7 @@ def test_pins_pass_unmutated():
 @pytest.mark.parametrize("mutation", [
     "transpose_rotation", "drop_cross_weight", "flip_shift_sign",
     "eps_not_squared", "gradient_one_sided", "swap_xz_sample",
+    "mask_strictly_above_half", "no_domain_slack", "no_clamp_onto_box", "lerp_weights_reversed",
 ])
 def test_planted_mistakes_are_caught(mutation, monkeypatch):
     if mutation == "transpose_rotation":
@@ -369,6 +529,20 @@ def test_planted_mistakes_are_caught(mutation, monkeypatch):
         orig_s = O.sample_points_f32
         monkeypatch.setattr(O, "sample_points_f32",
                             lambda R, dims: tuple(reversed(orig_s(R, dims))))
+    elif mutation == "mask_strictly_above_half":
+        monkeypatch.setattr(O, "_mask_on", lambda m: m > np.float32(0.5))
+    elif mutation == "no_domain_slack":
+        monkeypatch.setattr(O, "DOMAIN_SLACK", 0.0)
+    elif mutation == "no_clamp_onto_box":
+        def axis_bad(p, n):
+            slack = np.float32(O.DOMAIN_SLACK)
+            inside = (p >= -slack) & (p <= np.float32(n - 1) + slack)
+            i0 = np.minimum(np.floor(p).astype(np.int64), max(n - 2, 0))
+            t = (p - i0.astype(np.float32)).astype(np.float32)
+            return inside, i0, t
+        monkeypatch.setattr(O, "_axis_setup", axis_bad)
+    elif mutation == "lerp_weights_reversed":
+        monkeypatch.setattr(O, "_lerp", lambda a, b, t: (b + t * (a - b)).astype(np.float32))
     assert not _pins_pass(), f"mutation {mutation} went unnoticed"
 
 
