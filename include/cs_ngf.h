@@ -254,6 +254,11 @@ int64_t cs_ngf_launch_count(void);
  *   quats               host float64 [R][4] (w, x, y, z), read during the call
  *   best_score          device float32 [R]
  *   best_shift          device int32 [R][3]
+ * Every array pointer must be device (or managed) memory of the CURRENT
+ * device, which runs the work with its own copy of the scratch array; a host
+ * pointer or one on another device is rejected with EINVAL.  The caller
+ * guarantees the sizes: the library reads nz*ny*nx elements of each volume
+ * and writes R scores and R shifts.
  * Work is enqueued on `stream` and the call returns without waiting for it.
  * The first call on a device does a set-up step with that device current: it
  * looks up the device address of the scratch array.  Make that first call

@@ -238,6 +238,28 @@ def _dev_ptr(t, dtype, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_shapes(dims, named):
+    """Every (tensor, name) must have shape ``dims`` (checked before any pointer
+    reaches the library, which reads them with those dims)."""
+    for t, name in named:
+        if tuple(t.shape) != tuple(dims):
+            raise ValueError(f"{name} must have shape {tuple(dims)}, got {tuple(t.shape)}")
+
+
+def _check_outputs(out_score, out_shift, R):
+    """Caller-given outputs must hold R scores and R x 3 shifts."""
+    if out_score is not None and tuple(out_score.shape) != (R,):
+        raise ValueError(f"best_score must have shape ({R},), got {tuple(out_score.shape)}")
+    if out_shift is not None and tuple(out_shift.shape) != (R, 3):
+        raise ValueError(f"best_shift must have shape ({R}, 3), got {tuple(out_shift.shape)}")
+
+
+def _same_device(device, named):
+    for t, name in named:
+        if t.device != device:
+            raise ValueError(f"{name} is on {t.device}, expected {device}")
+
+
 def _quats(q) -> np.ndarray:
     q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(-1, 4))
     return q
@@ -274,6 +296,10 @@ class Fixed:
         self.measure = measure
         self.precision = precision
         self.pad_mode = pad_mode
+        # everything besides A and maskA that decides the handle's results
+        self.settings = dict(eps=float(eps), gamma=float(gamma), measure=measure,
+                             precision=precision, pad_mode=pad_mode, batch=int(batch),
+                             pad=tuple(int(v) for v in pad) if pad is not None else None)
         dims = (ctypes.c_int32 * 3)(*self.dims)
         h = ctypes.c_void_p()
         st = _check(_lib.cs_ngf_prepare_fixed(_dev_ptr(A, torch.float32, "A"),
@@ -322,7 +348,9 @@ class Fixed:
         import torch
         if tuple(B.shape) != self.dims or tuple(MB.shape) != self.dims:
             raise ValueError("B and maskB must have the fixed volume's shape")
-        return _dev_ptr(B, torch.float32, "B"), _dev_ptr(MB, torch.uint8, "maskB")
+        pb, pm = _dev_ptr(B, torch.float32, "B"), _dev_ptr(MB, torch.uint8, "maskB")
+        _same_device(self._keep[0].device, ((B, "B"), (MB, "maskB")))
+        return pb, pm
 
     def score_rotations(self, B, MB, quats, out_score=None, out_shift=None, stream=None):
         """Per-rotation best score [R] (float32) and shift [R, 3] (int32, z y x)."""
@@ -330,6 +358,7 @@ class Fixed:
         q = _quats(quats)
         R = q.shape[0]
         pb, pm = self._check_vol(B, MB)
+        _check_outputs(out_score, out_shift, R)
         if out_score is None:
             out_score = torch.empty(R, dtype=torch.float32, device=B.device)
         if out_shift is None:
@@ -441,24 +470,33 @@ def score_rotations_noalloc(A, MA, B, MB, quats, eps=1e-5, gamma=0.5, out_score=
     must not overlap on the GPU.  The outputs are allocated here by torch
     unless given."""
     import torch
+    if len(A.shape) != 3:
+        raise ValueError("A must be [nz][ny][nx]")
+    dims = tuple(int(d) for d in A.shape)
+    _check_shapes(dims, ((MA, "maskA"), (B, "B"), (MB, "maskB")))
+    q = _quats(quats)
+    R = q.shape[0]
+    _check_outputs(out_score, out_shift, R)
     for t, dt, name in ((A, torch.float32, "A"), (MA, torch.uint8, "maskA"),
                         (B, torch.float32, "B"), (MB, torch.uint8, "maskB")):
         _dev_ptr(t, dt, name)
-    dims = tuple(int(d) for d in A.shape)
-    q = _quats(quats)
-    R = q.shape[0]
-    if out_score is None:
-        out_score = torch.empty(R, dtype=torch.float32, device=A.device)
-    if out_shift is None:
-        out_shift = torch.empty((R, 3), dtype=torch.int32, device=A.device)
-    d = (ctypes.c_int32 * 3)(*dims)
-    _check(_lib.cs_ngf_score_rotations_noalloc(
-        _dev_ptr(A, torch.float32, "A"), _dev_ptr(MA, torch.uint8, "maskA"),
-        _dev_ptr(B, torch.float32, "B"), _dev_ptr(MB, torch.uint8, "maskB"), d,
-        float(eps), float(gamma), q.ctypes.data_as(ctypes.c_void_p), R,
-        _dev_ptr(out_score, torch.float32, "best_score"),
-        _dev_ptr(out_shift, torch.int32, "best_shift"), _stream_ptr(stream)),
-        "cs_ngf_score_rotations_noalloc")
+    named = [(MA, "maskA"), (B, "B"), (MB, "maskB")]
+    named += [(t, n) for t, n in ((out_score, "best_score"), (out_shift, "best_shift")) if t is not None]
+    _same_device(A.device, named)
+    # the library scores on the current device with that device's scratch
+    with torch.cuda.device(A.device):
+        if out_score is None:
+            out_score = torch.empty(R, dtype=torch.float32, device=A.device)
+        if out_shift is None:
+            out_shift = torch.empty((R, 3), dtype=torch.int32, device=A.device)
+        d = (ctypes.c_int32 * 3)(*dims)
+        _check(_lib.cs_ngf_score_rotations_noalloc(
+            _dev_ptr(A, torch.float32, "A"), _dev_ptr(MA, torch.uint8, "maskA"),
+            _dev_ptr(B, torch.float32, "B"), _dev_ptr(MB, torch.uint8, "maskB"), d,
+            float(eps), float(gamma), q.ctypes.data_as(ctypes.c_void_p), R,
+            _dev_ptr(out_score, torch.float32, "best_score"),
+            _dev_ptr(out_shift, torch.int32, "best_shift"), _stream_ptr(stream)),
+            "cs_ngf_score_rotations_noalloc")
     return out_score, out_shift
 
 

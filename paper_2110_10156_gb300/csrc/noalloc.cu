@@ -148,6 +148,24 @@ int na_pad(int n) {
     default: break;                                \
   }
 
+// a pointer the kernels will dereference must be device (or managed) memory
+// of the device that runs them; anything else would fault instead of failing
+cs_ngf_status na_check_ptr(const void* p, int device, const char* name) {
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return na_fail(CS_NGF_EINVAL, std::string(name) + ": cudaPointerGetAttributes: " +
+                                      cudaGetErrorString(e));
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return na_fail(CS_NGF_EINVAL, std::string(name) + " is not device memory");
+  if (at.device != device)
+    return na_fail(CS_NGF_EINVAL, std::string(name) + " is on device " + std::to_string(at.device) +
+                                      ", but device " + std::to_string(device) + " is current");
+  return CS_NGF_OK;
+}
+
 cs_ngf_status na_launched(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(CS_NGF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -183,6 +201,12 @@ extern "C" cs_ngf_status cs_ngf_score_rotations_noalloc(
   int device = 0;
   NA_CUDA(cudaGetDevice(&device));
   if (device < 0 || device >= kMaxDevices) return na_fail(CS_NGF_EINVAL, "device ordinal out of range");
+  {
+    const void* ptrs[6] = {A, maskA, B, maskB, best_score, best_shift};
+    const char* names[6] = {"A", "maskA", "B", "maskB", "best_score", "best_shift"};
+    for (int i = 0; i < 6; ++i)
+      if (cs_ngf_status s = na_check_ptr(ptrs[i], device, names[i])) return s;
+  }
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_na_mutex);

@@ -59,3 +59,24 @@ def test_numpy_arrays_are_refused(cs):
         cs.score_rotations_noalloc(A, M, A, M, np.array([[1.0, 0.0, 0.0, 0.0]]))
     with pytest.raises(TypeError, match="CUDA tensor"):
         cs.global_align(A, M, A, M)
+
+
+def test_noalloc_refuses_mismatched_shapes_and_outputs_before_any_launch(cs):
+    """The allocation-free call reads B and the masks with A's dims and writes
+    R results, so the binding refuses any other shape up front (these host
+    tensors would be refused later too; the shape check comes first)."""
+    A, M = _host_pair()
+    q = np.array([[1.0, 0.0, 0.0, 0.0]] * 2)
+    small = torch.zeros((8, 8, 7), dtype=torch.float32)
+    with pytest.raises(ValueError, match="shape"):
+        cs.score_rotations_noalloc(A, M, small, M, q)
+    with pytest.raises(ValueError, match="shape"):
+        cs.score_rotations_noalloc(A, M, A, torch.ones((8, 7, 8), dtype=torch.uint8), q)
+    with pytest.raises(ValueError, match="shape"):
+        cs.score_rotations_noalloc(A, torch.ones((9, 8, 8), dtype=torch.uint8), A, M, q)
+    with pytest.raises(ValueError, match="nz"):
+        cs.score_rotations_noalloc(A[0], M[0], A[0], M[0], q)
+    with pytest.raises(ValueError, match="best_score"):
+        cs.score_rotations_noalloc(A, M, A, M, q, out_score=torch.zeros(1))
+    with pytest.raises(ValueError, match="best_shift"):
+        cs.score_rotations_noalloc(A, M, A, M, q, out_shift=torch.zeros((2, 2), dtype=torch.int32))

@@ -88,3 +88,48 @@ def test_bad_chunk(tmp_path, quats):
     with pytest.raises(ValueError):
         resume.score_rotations_resumable(FakeScorer(), None, None, quats, str(tmp_path / "c.npz"),
                                          chunk=0)
+
+
+def test_a_checkpoint_for_other_volumes_or_settings_is_refused(tmp_path, quats):
+    """Same rotations, chunk and shape, but a different B, mask, fixed volume
+    or scoring setting: the saved chunks must not be merged in."""
+    path = str(tmp_path / "ck.npz")
+    rng = np.random.default_rng(3)
+    B = rng.random((16, 16, 16)).astype(np.float32)
+    MB = np.ones((16, 16, 16), np.uint8)
+    f = FakeScorer()
+    f._keep = (rng.random((16, 16, 16)).astype(np.float32), MB)
+    f.settings = dict(eps=1e-5, gamma=0.5)
+    resume.score_rotations_resumable(f, B, MB, quats[:5], path, chunk=5)
+    B2 = B.copy()
+    B2[3, 4, 5] += 1.0
+    with pytest.raises(ValueError, match="another job"):
+        resume.score_rotations_resumable(f, B2, MB, quats[:5], path, chunk=5)
+    MB2 = MB.copy()
+    MB2[0, 0, 0] = 0
+    with pytest.raises(ValueError, match="another job"):
+        resume.score_rotations_resumable(f, B, MB2, quats[:5], path, chunk=5)
+    g = FakeScorer()
+    g._keep = (f._keep[0] + 1.0, MB)
+    g.settings = f.settings
+    with pytest.raises(ValueError, match="another job"):
+        resume.score_rotations_resumable(g, B, MB, quats[:5], path, chunk=5)
+    h = FakeScorer()
+    h._keep = f._keep
+    h.settings = dict(eps=1e-5, gamma=0.6)
+    with pytest.raises(ValueError, match="another job"):
+        resume.score_rotations_resumable(h, B, MB, quats[:5], path, chunk=5)
+    # the same job again reuses the finished checkpoint as it stands
+    again = FakeScorer()
+    again._keep, again.settings = f._keep, f.settings
+    resume.score_rotations_resumable(again, B, MB, quats[:5], path, chunk=5)
+    assert again.scored == 0
+
+
+def test_a_truncated_checkpoint_is_refused_with_a_message(tmp_path, quats):
+    path = tmp_path / "ck.npz"
+    resume.score_rotations_resumable(FakeScorer(), None, None, quats, str(path), chunk=5)
+    data = path.read_bytes()
+    path.write_bytes(data[: len(data) // 2])
+    with pytest.raises(ValueError, match="not a readable checkpoint"):
+        resume.score_rotations_resumable(FakeScorer(), None, None, quats, str(path), chunk=5)

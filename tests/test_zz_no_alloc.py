@@ -13,8 +13,9 @@ failure has already run every other test.
 import numpy as np
 import pytest
 
+from oracle import cs_ngf_oracle as O
 from paper_2110_10156_gb300 import synth
-from tests.parity_util import TAU_FP32
+from tests.parity_util import TAU_FP32, check_best_against_map
 
 pytestmark = pytest.mark.gpu
 
@@ -79,3 +80,33 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(cs):
         cs.score_rotations_noalloc(A, M, A, M, [[1.0, 0, 0, 0]])
     assert e.value.status == cs.EINVAL
     assert "32" in str(e.value)
+
+
+def _compare_with_oracle(cs, p, eps=1e-5, gamma=0.5):
+    """Per rotation, the gap rule against the FP64 oracle's full map."""
+    sc, sh = cs.score_rotations_noalloc(dev(p.A), dev(p.MA), dev(p.B), dev(p.MB), p.quats,
+                                        eps=eps, gamma=gamma)
+    sc, sh = sc.cpu().numpy(), sh.cpu().numpy()
+    kinds = []
+    for r, q in enumerate(p.quats):
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, eps=eps, gamma=gamma)
+        kinds.append(check_best_against_map(omap, sc[r], sh[r], tau=TAU_FP32))
+    return kinds
+
+
+def test_noalloc_against_the_oracle_32_cubed_and_ragged(cs):
+    kinds = _compare_with_oracle(cs, synth.config_pair(0))
+    assert kinds.count("exact") >= 6
+    kinds = _compare_with_oracle(cs, synth.small_pair(78, (20, 17, 23), n_rot=4))
+    assert "exact" in kinds
+
+
+@pytest.mark.parametrize("dims", [(8, 5, 12), (2, 16, 3), (16, 9, 2)])
+def test_noalloc_every_fft_length_against_handle_and_oracle(cs, dims):
+    """Mixed small sizes, so that the 16-, 32- and 64-point arms of the
+    allocation-free path all run (2n - 1 <= 16, <= 32, <= 64), including the
+    smallest size (2) on an axis."""
+    p = synth.small_pair(200 + sum(dims), dims, n_rot=4, masks="full", max_shift=1)
+    _compare_with_handle(cs, p)
+    _compare_with_oracle(cs, p)
+
