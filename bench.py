@@ -130,10 +130,11 @@ def stage_bytes(dims, pad, nb, stage, nch=3, precision="fp32"):
 
     nch packed channel fields per rotation (3 for the squared measure; BF16 or
     FP32 storage) plus one mask field per pair of rotations (FP32).  The z pass
-    counts its field reads and the fixed-spectra tile it loads once per launch;
-    its output planes and the inverse passes' traffic depend on the slab bound
-    and are left out of the z pass (a lower bound) and counted unpruned for the
-    two inverse passes (an upper bound)."""
+    counts its field reads, the fixed-spectra tile it loads once per launch and
+    its output F2, min(2n - 1, P) planes of Z = X + iY per rotation (the z
+    inverse writes only the planes the slab bound admits, so this is an upper
+    bound; "zmac_no_f2" leaves F2 out, a lower bound).  The inverse passes are
+    counted unpruned (an upper bound)."""
     nz, ny, nx = dims
     Pz, Py, Px = pad
     vz, vy = 2 * nz - 1, 2 * ny - 1
@@ -142,14 +143,15 @@ def stage_bytes(dims, pad, nb, stage, nch=3, precision="fp32"):
     per_elem = nch * nb * cb + ((nb + 1) // 2) * 8     # bytes per element position, all fields
     F0 = per_elem * nz * ny * Px
     F1 = per_elem * nz * Px * Py
-    F2 = vz * Px * Py * 8
-    F3 = vz * vy * Px * 8
+    F2 = min(vz, Pz) * Px * Py * 8
+    F3 = min(vz, Pz) * min(vy, Py) * Px * 8
     UV = (2 * nch + 1) * (Px // 2 + 1) * Py * Pz * 8
     return {
         "resample": nb * nvox * 5,
         "fwd_x": nb * nvox * 5 + F0,
         "fwd_y": F0 + F1,
-        "zmac": F1 + UV,
+        "zmac": F1 + UV + nb * F2,
+        "zmac_no_f2": F1 + UV,
         "inv_y": nb * (F2 + F3),
         "inv_x": nb * F3,
     }.get(stage, 0)
@@ -280,6 +282,51 @@ def host_cores():
 
 
 # ------------------------------------------------------------------ arms
+def l2_note(roofline_step, R, batch):
+    if roofline_step is not None:
+        tb = roofline_step["dram_bytes_per_rotation"] * R / 1e12
+        return (f"inputs larger than L2: each launch group's FFT intermediates exceed the 129 MB L2; "
+                f"about {tb:.2f} TB of DRAM traffic per step (ncu bytes per rotation x {R})")
+    return ("inputs larger than L2: each launch group's FFT intermediates "
+            f"({batch} rotations) exceed the 129 MB L2")
+
+
+def time_form(cs_ngf, A, MA, B, MB, quats, precision, args, fp32_value):
+    """One precision form on the headline workload: the same step, warm-up and
+    timed steps (CUDA events on the launching stream) as the FP32 line, then
+    one scoring call for the per-rotation results.  Returns (summary dict,
+    (scores, shifts) as numpy)."""
+    import torch
+    g = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=precision, pad_mode=args.pad_mode,
+                             autotune=args.autotune == "on")
+
+    def step():
+        g.update_fixed(A, MA)
+        return g.align(B, MB, quats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = len(quats) * args.steps / (ms / 1000.0)
+    sc, sh = g.score_rotations(B, MB, quats)
+    out = (sc.cpu().numpy(), sh.cpu().numpy())
+    summary = {"value": value, "unit": UNIT, "ms_per_step": ms / args.steps,
+               "ratio_to_fp32": value / fp32_value, "steps": args.steps,
+               "storage": f"{precision} channel fields of the forward x and y passes; mask / overlap "
+                          "path and everything after the spectral sum FP32",
+               "result": {"best_rotation": res[1], "shift": list(res[2]), "score": res[0]}}
+    g.release()
+    return summary, out
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,11 +352,14 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * total / args.steps * (args.rotations / sample),
+        "ms_per_step": 1000.0 * total / args.steps,
+        "ms_per_workload_extrapolated": 1000.0 * total / args.steps * (args.rotations / sample),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "volume": [150, 150, 150], "fft": [320, 320, 320],
-                   "rotations": args.rotations, "sample_rotations_per_step": sample},
+                   "rotations": args.rotations, "sample_rotations_per_step": sample,
+                   "step": f"{sample} rotations of the workload scored by the oracle (one per "
+                           "process); ms_per_step is that sample's time"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{sample} of the {args.rotations} rotations per step, one per "
                                    f"process, FP64 numpy FFT form at 320^3"},
@@ -444,6 +494,12 @@ def run_ours(args):
                 "traffic": None if tr is None else tr * per_launch_rot,
                 "algorithmic_bytes_per_launch": total_bytes / (prof_steps * nbatches),
                 "timing": "CUDA events around every launch of one profiled step after the timed region"}
+    if dom == "zmac":               # the same without the F2 writes (a lower bound)
+        lo = sum(stage_bytes(dims, cp, nb, "zmac_no_f2", precision=args.precision)
+                 for cp, nb in launches_of) * prof_steps
+        ach_lo = lo / (stage_ms[dom] / 1000.0) / 1e9 if stage_ms[dom] > 0 else 0.0
+        roofline.update({"achieved_without_f2": ach_lo, "frac_without_f2": ach_lo / peak,
+                         "model": "F1 read + F2 write (min(2n-1, P) planes) + fixed tile per launch"})
 
     # the whole step against HBM: the ncu DRAM bytes per rotation of every
     # scoring stage (same kernel sources and precision only), times the
@@ -467,6 +523,18 @@ def run_ours(args):
                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                         "flops_per_launch": fl / (prof_steps * nbatches)}
 
+    # ---------------- the reduced-precision forms on the same workload and
+    # launch configuration (ratio to the FP32 value above)
+    forms, form_results = {}, {}
+    if ws == 1 and args.precision == "fp32" and not args.no_forms:
+        fs = ClockSampler(local)
+        fs.start()
+        for prec in ("bf16", "fp16"):
+            forms[prec], form_results[prec] = time_form(cs_ngf, A, MA, B, MB, quats, prec, args, value)
+        fclk = fs.stop()
+        for prec in forms:
+            forms[prec]["clocks"] = fclk
+
     cpu = None
     oracle_check = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -480,6 +548,16 @@ def run_ours(args):
             oracle_check = compare_with_oracle(out_s, out_c, best)
         except Exception as exc:  # reporting only: never fails the run
             oracle_check = {"error": repr(exc)}
+        for prec, (fsc, fsh) in form_results.items():
+            try:
+                forms[prec]["oracle_check"] = compare_with_oracle(fsc, fsh, best)
+            except Exception as exc:
+                forms[prec]["oracle_check"] = {"error": repr(exc)}
+    f.release()
+
+    serving = None
+    if rank == 0 and ws == 1 and not args.no_serving:
+        serving = {prec: serving_measure(args, prec) for prec in ("fp32", "bf16")}
 
     if rank == 0:
         line = {
@@ -497,7 +575,7 @@ def run_ours(args):
                                    "split": list(e["splits"][e["variant"]]),
                                    "ms": [round(v, 3) for v in e["ms"]]} for e in cs_ngf.tuning()],
                        "rotations_per_gpu": R, "batch": f.batch, "masks": "thresholded foreground",
-                       "l2": "inputs larger than L2: every step streams >1 TB of FFT intermediates",
+                       "l2": l2_note(roofline_step, R, f.batch),
                        "step": "update_fixed + score all rotations + max over rotations"},
             "roofline": roofline, "roofline_alu": roofline_alu, "roofline_step": roofline_step,
             "cpu_baseline": cpu,
@@ -509,9 +587,10 @@ def run_ours(args):
             "stages_ms_per_step": {k: v / prof_steps for k, v in stage_ms.items()},
             "profiled_step_ms": prof_step_ms,
             "result": {"best_rotation": res[1], "shift": list(res[2]), "score": res[0]},
+            "forms": forms or None,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    f.release()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -678,9 +757,10 @@ def serve_pair(shape):
     return d
 
 
-def run_serving(args):
+def serving_measure(args, precision="fp32"):
     """Poisson arrivals of mixed-size jobs, 200-2000 rotations each, through the
-    continuous-batching server; p50/p99 job latency and rotations/s."""
+    continuous-batching server at the offered load: p50/p99 job latency (ms)
+    and rotations/s."""
     from paper_2110_10156_gb300 import cs_ngf, synth
     rng = np.random.default_rng(1003)
     pairs = {s: serve_pair(s) for s in SERVE_SHAPES}
@@ -698,7 +778,8 @@ def run_serving(args):
         p = pairs[s]
         q = synth.random_quaternions(rng, 128)
         t0 = time.perf_counter()
-        srv.wait(srv.submit(p["A"], p["MA"], p["B"], p["MB"], q), per_rotation=False)
+        srv.wait(srv.submit(p["A"], p["MA"], p["B"], p["MB"], q, precision=precision),
+                 per_rotation=False)
         svc[s] = (time.perf_counter() - t0) / 128
     mean_service = float(np.mean([svc[s] * len(q) for s, q in jobs]))
     lam = args.serve_load / mean_service                  # jobs per second
@@ -708,22 +789,33 @@ def run_serving(args):
     for (s, q), gap in zip(jobs, gaps):
         time.sleep(float(gap))
         p = pairs[s]
-        ids.append(srv.submit(p["A"], p["MA"], p["B"], p["MB"], q))
+        ids.append(srv.submit(p["A"], p["MA"], p["B"], p["MB"], q, precision=precision))
     res = [srv.wait(j, per_rotation=False) for j in ids]
     wall = time.perf_counter() - t_start
     srv.close()
     lat = np.array([r["latency_ms"] for r in res])
     rot = sum(len(q) for _, q in jobs)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "rotations_per_s": rot / wall, "precision": precision,
+            "config": {"workload": "jobs of 64^3, 96x128x128, 150^3, 192x192x160 with 200-2000 rotations",
+                       "jobs": n_jobs, "offered_load": args.serve_load, "arrival_rate_per_s": lam,
+                       "max_active_jobs": args.serve_active, "batch": args.serve_batch,
+                       "admission": args.serve_policy},
+            "service_ms_per_rotation_alone": {"x".join(map(str, s)): 1000 * v for s, v in svc.items()},
+            "statuses": sorted(set(r["status"] for r in res))}
+
+
+def run_serving(args):
+    """--workload serve: the serving measurement as its own JSON line."""
+    m = serving_measure(args, args.precision)
     print(json.dumps({
         "metric": "serving: p50/p99 job latency and rotations/s, mixed sizes, Poisson arrivals",
-        "unit": "ms", "value": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "rotations_per_s": rot / wall, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "jobs of 64^3, 96x128x128, 150^3, 192x192x160 with 200-2000 rotations",
-                   "jobs": n_jobs, "offered_load": args.serve_load, "arrival_rate_per_s": lam,
-                   "max_active_jobs": args.serve_active, "batch": args.serve_batch,
-                   "admission": args.serve_policy},
-        "service_ms_per_rotation_alone": {"x".join(map(str, s)): 1000 * v for s, v in svc.items()},
-        "statuses": sorted(set(r["status"] for r in res))}), flush=True)
+        "unit": "ms", "value": m["p50_ms"], "p99_ms": m["p99_ms"],
+        "rotations_per_s": m["rotations_per_s"], "higher_is_better": False,
+        "dtype": "f32" if args.precision == "fp32" else f"f32 arithmetic, {args.precision} channel intermediates",
+        "data": "synthetic", "config": m["config"],
+        "service_ms_per_rotation_alone": m["service_ms_per_rotation_alone"],
+        "statuses": m["statuses"]}), flush=True)
     return 0
 
 
@@ -744,6 +836,10 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=16,
                     help="oracle rotations per CPU step (at most one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the BF16 and FP16 forms' sub-results of the headline line")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving sub-result (p50/p99) of the headline line")
     ap.add_argument("--tab3-direct-max", type=int, default=16)
     ap.add_argument("--search-seed", type=int, default=2021)
     ap.add_argument("--workload", choices=("align150", "small32", "serve", "large256", "tab3", "search150"),

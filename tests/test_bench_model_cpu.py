@@ -39,12 +39,18 @@ def test_byte_model_at_the_headline_lengths(bench):
     assert per("fwd_x") == pytest.approx(nvox * 5 + F0)
     assert per("fwd_y") == pytest.approx(F0 + F1)
     UV = 7 * 101 * 200 * 200 * 8                 # fixed spectra, loaded once per launch
-    assert per("zmac") == pytest.approx(F1 + UV / nb)
-    F2, F3 = 299 * 200 * 200 * 8, 299 * 299 * 200 * 8
+    # the z inverse's output: min(2n - 1, P) = 200 planes of Z per (kx, ky) column
+    F2 = 200 * 200 * 200 * 8
+    assert per("zmac") == pytest.approx(F1 + UV / nb + F2)
+    assert per("zmac_no_f2") == pytest.approx(F1 + UV / nb)
+    F3 = 200 * 200 * 200 * 8                     # [vz][vy][kx], again at most P planes and rows
     assert per("inv_y") == F2 + F3 and per("inv_x") == F3
     # the figures the design notes quote (MB per rotation)
     assert round(per("fwd_x") / 1e6) == 143 and round(per("fwd_y") / 1e6) == 294
-    assert round(per("zmac") / 1e6) == 175
+    assert round(per("zmac") / 1e6) == 239 and round(per("zmac_no_f2") / 1e6) == 175
+    # at full padding every one of the 2n - 1 = 299 shifts has a plane
+    full = lambda st: bench.stage_bytes(dims, (320, 320, 320), nb, st) / nb
+    assert full("inv_x") == 299 * 299 * 320 * 8
 
 
 def test_byte_model_halves_channel_bytes_in_16_bit_forms(bench):
@@ -133,6 +139,8 @@ def test_reference_arm_prints_one_line(bench, monkeypatch, capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["higher_is_better"] is True
     assert line["value"] == pytest.approx(2.0)      # 4 rotations per 2 s step
+    assert line["ms_per_step"] == pytest.approx(2000.0)    # the sample actually timed
+    assert line["ms_per_workload_extrapolated"] == pytest.approx(2000.0 * 1000 / 4)
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle"
 

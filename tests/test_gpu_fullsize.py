@@ -7,7 +7,8 @@ import pytest
 
 from oracle import cs_ngf_oracle as O
 from paper_2110_10156_gb300 import synth
-from tests.parity_util import check_best_against_map, check_best_at_sampled_shifts, face_neighbours
+from tests.parity_util import (check_best_against_map, check_best_at_sampled_shifts, check_maps,
+                               face_neighbours)
 
 pytestmark = pytest.mark.gpu
 
@@ -69,6 +70,25 @@ def test_150_cubed_1000_rotations(cs, pair150, oracle150, precision, tau, pad_mo
     # sampled rotations against the oracle's full map (FFT form at 320^3)
     for r, omap in oracle150.items():
         check_best_against_map(omap, sc[r], sh[r], tau=tau)
+    f.release()
+
+
+@pytest.mark.parametrize("precision,tau", [("fp32", 1e-4), ("bf16", 1e-2), ("fp16", 1e-2)])
+def test_150_cubed_whole_maps_at_bound_limited_lengths(cs, pair150, oracle150, precision, tau):
+    """Eq. 5 for every shift of the 150^3 pair, element by element against the
+    oracle's full-length map, at the lengths the bench runs most rotations at
+    (bound-limited, e.g. 200 per axis with n = 150 > P/2: the unpruned first
+    stage and the shared-memory NGF slots of the x pass, the two-field z
+    pass).  The valid sets must be identical and the error within tau of the
+    largest score."""
+    p = pair150
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), precision=precision)
+    B, MB = dev(p.B), dev(p.MB)
+    for r, omap in oracle150.items():
+        gmap = f.score_map(B, MB, p.quats[r]).cpu().numpy()
+        assert all(v < 320 for v in f.pad) and max(f.pad) < 2 * 150 - 1, f.pad
+        assert 2 * 150 > min(f.pad)             # n > P/2 on some axis: unpruned first stage
+        check_maps(omap, gmap, tau)
     f.release()
 
 
