@@ -133,6 +133,15 @@ typedef struct {
                         whose timings choose differently.
                         2: every pass uses the alternative split wherever its length has
                         one, without timing (for tests and comparisons). */
+  int32_t tensor_cores; /* 1 (cs_ngf_default_config): in the BF16 and FP16 forms the z pass
+                        runs the forward z-axis DFT of the NGF channel fields on the tensor
+                        cores (BF16 / FP16 operands, FP32 accumulation; Eq. 7-8 unchanged)
+                        wherever the z length is at most 254 and has a split of at least
+                        8 columns (32, 40, 64, 80, 100, 128, 160, 200); the mask field and
+                        every inverse transform stay FP32 on the CUDA cores.  0: the CUDA-core
+                        FFT for every field.  Ignored in the FP32 form.  A tensor-core pass
+                        that waits more than 2 s for its own MMAs stops; the next synchronous
+                        call (cs_ngf_align, cs_ngf_score_rotations_host) then returns ECUDA. */
 } cs_ngf_config;
 
 typedef struct {
@@ -149,7 +158,8 @@ typedef struct {
 } cs_ngf_info;
 
 /* Fill *cfg with the paper's settings (eps 1e-5, gamma 0.5, automatic pad and
- * batch) and bound-limited padding. */
+ * batch), bound-limited padding and the tensor-core z pass of the
+ * reduced-precision forms. */
 void cs_ngf_default_config(cs_ngf_config* cfg);
 
 /* Section 3.1, Eq. 1, 6-8, A side: the NGF of the fixed volume A, its six

@@ -43,7 +43,8 @@ STAGES = ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x", "fixed", "othe
 class Config(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("pad", ctypes.c_int32 * 3), ("batch", ctypes.c_int32), ("measure", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("pad_mode", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("pad_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("tensor_cores", ctypes.c_int32)]
 
 
 class TuningEntry(ctypes.Structure):
@@ -269,10 +270,13 @@ class Fixed:
     """Handle on the device-resident fixed-volume spectra (cs_ngf_prepare_fixed)."""
 
     def __init__(self, A, MA, eps=1e-5, gamma=0.5, pad=None, batch=0, stream=None,
-                 measure="squared", precision="fp32", pad_mode="bound", autotune=False):
+                 measure="squared", precision="fp32", pad_mode="bound", autotune=False,
+                 tensor_cores=True):
         """autotune: False (built-in radix splits), True (timed on first use
         at new lengths) or "alternative" (the second split wherever a length
-        has one)."""
+        has one).  tensor_cores: the BF16 and FP16 forms run the z-axis
+        forward DFT of the channel fields on the tensor cores (False: CUDA-core
+        FFTs throughout)."""
         import torch
         _dev_ptr(A, torch.float32, "A")
         _dev_ptr(MA, torch.uint8, "maskA")
@@ -293,12 +297,14 @@ class Fixed:
         cfg.precision = PRECISIONS[precision]
         cfg.pad_mode = PAD_MODES[pad_mode]
         cfg.autotune = 2 if autotune == "alternative" else (1 if autotune else 0)
+        cfg.tensor_cores = 1 if tensor_cores else 0
         self.measure = measure
         self.precision = precision
         self.pad_mode = pad_mode
         # everything besides A and maskA that decides the handle's results
         self.settings = dict(eps=float(eps), gamma=float(gamma), measure=measure,
                              precision=precision, pad_mode=pad_mode, batch=int(batch),
+                             tensor_cores=bool(tensor_cores),
                              pad=tuple(int(v) for v in pad) if pad is not None else None)
         dims = (ctypes.c_int32 * 3)(*self.dims)
         h = ctypes.c_void_p()
@@ -524,7 +530,7 @@ class Server:
         self._R = {}
 
     def submit(self, A, MA, B, MB, quats, eps=1e-5, gamma=0.5, pad=None, batch=0,
-               measure="squared", precision="fp32", pad_mode="bound") -> int:
+               measure="squared", precision="fp32", pad_mode="bound", tensor_cores=True) -> int:
         arrs = []
         for name, a, dt in (("A", A, np.float32), ("maskA", MA, np.uint8), ("B", B, np.float32),
                             ("maskB", MB, np.uint8)):
@@ -539,6 +545,7 @@ class Server:
         cfg.measure = MEASURES[measure]
         cfg.precision = PRECISIONS[precision]
         cfg.pad_mode = PAD_MODES[pad_mode]
+        cfg.tensor_cores = 1 if tensor_cores else 0
         if pad is not None:
             for i, p in enumerate(pad):
                 cfg.pad[i] = int(p)

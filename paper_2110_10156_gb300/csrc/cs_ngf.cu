@@ -160,6 +160,18 @@ cs_ngf_status check_launch(const char* what) {
   return CS_NGF_OK;
 }
 
+// ECUDA (once) if a tensor-core pass of this handle stopped on its bounded
+// wait since the last check; `st` has been synchronised by the caller
+cs_ngf_status tc_status(cs_ngf_fixed* f, cudaStream_t st) {
+  if (!f->tc_err) return CS_NGF_OK;
+  int flag = 0;
+  CS_CUDA(cudaMemcpyAsync(&flag, f->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CS_CUDA(cudaStreamSynchronize(st));
+  if (!flag) return CS_NGF_OK;
+  CS_CUDA(cudaMemsetAsync(f->tc_err, 0, sizeof(int), st));
+  return fail(CS_NGF_ECUDA, "a tensor-core z pass timed out waiting for its MMAs; its results are invalid");
+}
+
 void free_handle(cs_ngf_fixed* f) {
   if (!f) return;
   DeviceGuard guard(f->device);
@@ -176,6 +188,7 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->bounds);
   cudaFree(f->thr);
   cudaFree(f->keys);
+  cudaFree(f->tc_err);
   for (int a = 0; a < 3; ++a) {
     bool dup = false;
     for (int b = 0; b < a; ++b) dup |= (f->tw[b] == f->tw[a]);
@@ -822,6 +835,7 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
   if (cfg.pad_mode != CS_NGF_PAD_FULL && cfg.pad_mode != CS_NGF_PAD_BOUND)
     return fail(CS_NGF_EINVAL, "unknown pad_mode");
   if (cfg.autotune < 0 || cfg.autotune > 2) return fail(CS_NGF_EINVAL, "autotune must be 0, 1 or 2");
+  if (cfg.tensor_cores != 0 && cfg.tensor_cores != 1) return fail(CS_NGF_EINVAL, "tensor_cores must be 0 or 1");
   for (int a = 0; a < 3; ++a) {
     pad[a] = cfg.pad[a] ? cfg.pad[a] : auto_pad(dims[a]);
     if (!pad_supported(pad[a]))
@@ -912,12 +926,15 @@ size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int meas
 // ============================================================================
 extern "C" {
 
+static_assert(sizeof(cs_ngf_config) == 44, "cs_ngf_config layout (the Python binding mirrors it)");
+
 void cs_ngf_default_config(cs_ngf_config* cfg) {
   if (!cfg) return;
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->eps = 1e-5f;
   cfg->gamma = 0.5f;
   cfg->pad_mode = CS_NGF_PAD_BOUND;
+  cfg->tensor_cores = 1;
 }
 
 int32_t cs_ngf_auto_pad(int32_t n) { return (n >= 2 && n <= 256) ? auto_pad(n) : 0; }
@@ -965,6 +982,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   g.nf = g.nch + 1;
   g.store = cfg.precision == CS_NGF_BF16 ? kStoreBF16 : cfg.precision == CS_NGF_FP16 ? kStoreF16 : kStoreF32;
   set_field_scales(g);
+  g.tc = cfg.tensor_cores;
   for (int a = 0; a < 3; ++a) f->alloc_pad[a] = pad[a];
   f->pad_mode = cfg.pad_mode;
   f->autotune = cfg.autotune;
@@ -1009,6 +1027,9 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->bounds, (size_t)batch * 6));
   CS_TRYC(dalloc(&f->thr, (size_t)batch));
   CS_TRYC(dalloc(&f->keys, (size_t)batch));
+  CS_TRYC(dalloc(&f->tc_err, (size_t)1));
+  CS_TRYC(cudaMemsetAsync(f->tc_err, 0, sizeof(int), st));
+  g.tc_err = f->tc_err;
   f->fixed_bytes = uv_elems * sizeof(float2);
   f->workspace_bytes = (size_t)batch * per_rot + shared_ws;
   for (int a = 0; a < 3; ++a) {                 // one table per axis: the lengths may part
@@ -1061,7 +1082,7 @@ cs_ngf_status cs_ngf_score_rotations_host(cs_ngf_fixed* f, const float* B, const
   CS_CUDA(cudaMemcpyAsync(best_score, f->res_score, sizeof(float) * R, cudaMemcpyDeviceToHost, st));
   CS_CUDA(cudaMemcpyAsync(best_shift, f->res_shift, sizeof(int32_t) * 3 * R, cudaMemcpyDeviceToHost, st));
   CS_CUDA(cudaStreamSynchronize(st));
-  return CS_NGF_OK;
+  return tc_status(f, st);
 }
 
 cs_ngf_status cs_ngf_align(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
@@ -1080,6 +1101,7 @@ cs_ngf_status cs_ngf_align(cs_ngf_fixed* f, const float* B, const uint8_t* maskB
   CS_CUDA(cudaMemcpyAsync(sc.data(), f->res_score, sizeof(float) * R, cudaMemcpyDeviceToHost, st));
   CS_CUDA(cudaMemcpyAsync(sh.data(), f->res_shift, sizeof(int32_t) * 3 * R, cudaMemcpyDeviceToHost, st));
   CS_CUDA(cudaStreamSynchronize(st));
+  if (cs_ngf_status s = tc_status(f, st)) return s;
   int best = -1;
   for (int r = 0; r < R; ++r)
     if (std::isfinite(sc[r]) && (best < 0 || sc[r] > sc[best])) best = r;

@@ -59,6 +59,7 @@ struct cs_ngf_fixed {
   int* bounds = nullptr;       // per rotation of a batch: shift slots that can be valid
   float* thr = nullptr;
   unsigned long long* keys = nullptr;
+  int* tc_err = nullptr;       // set by a tensor-core pass that stopped on its bounded wait
   float2* tw[3] = {nullptr, nullptr, nullptr};   // z, y, x
   // rotation matrices: pinned host staging + device copy, grown on demand
   RotMat* rot_h = nullptr;

@@ -46,6 +46,12 @@ struct Geo {
   // scale0[j] (scale1[j]), a power of two that keeps it inside FP16's range;
   // 1 in the other forms and for the mask field (j = nch)
   float scale0[4], scale1[4];
+  // 1: in the BF16 and FP16 forms the z pass runs the forward z-axis DFT of
+  // the channel fields on the tensor cores (k_zmac_tc) where its length allows
+  int tc;
+  // set to 1 by a tensor-core pass whose bounded wait for its own MMAs ran out
+  // (it then stops and returns); nullptr: not reported
+  int* tc_err;
 };
 
 constexpr int kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2;

@@ -677,12 +677,28 @@ void launch_zmac_t(const void* F1, const float2* UV, float2* F2, const float2* t
   });
 }
 
+}  // namespace csngf
+
+#include "zmac_tc.cuh"
+
+namespace csngf {
+
 template <int P>
 void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw, Geo g, int nrot,
                  const int* bounds, cudaStream_t st, int v) {
   by_split<P>(v, [&](auto vc) {
     constexpr int V = decltype(vc)::value;
-    if (2 * g.nz <= P) launch_zmac_t<P, true, V>(F1, UV, F2, tw, g, nrot, bounds, st);
+    const bool half = 2 * g.nz <= P;
+    if (g.tc && g.store != kStoreF32) {          // reduced-precision forms: tensor-core z DFT
+      bool done = false;
+      by_store(g.store, [&](auto sf) {
+        constexpr int ST = decltype(sf)::value;
+        done = half ? launch_zmac_tc_t<P, ST, true, V>(F1, UV, F2, tw, g, nrot, bounds, st)
+                    : launch_zmac_tc_t<P, ST, false, V>(F1, UV, F2, tw, g, nrot, bounds, st);
+      });
+      if (done) return;
+    }
+    if (half) launch_zmac_t<P, true, V>(F1, UV, F2, tw, g, nrot, bounds, st);
     else launch_zmac_t<P, false, V>(F1, UV, F2, tw, g, nrot, bounds, st);
   });
 }

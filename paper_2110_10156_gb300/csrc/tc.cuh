@@ -1,0 +1,120 @@
+// Fifth-generation tensor-core primitives (sm_100 family, tcgen05) in inline
+// PTX: tensor-memory allocation, shared-memory matrix descriptors, the
+// single-thread MMA issue with completion signalled on an mbarrier, and the
+// warp-collective loads of the FP32 accumulator out of tensor memory.
+//
+// Shared-memory operand layout (no swizzle): an operand is a grid of "core
+// matrices" of 8 rows x 16 bytes (8 16-bit elements), each stored as 128
+// contiguous bytes.  K-major: a core matrix holds 8 rows (M or N) x 8
+// consecutive K elements.  MN-major: 8 consecutive K rows x 8 consecutive
+// M/N elements.  In both, the descriptor's leading-byte offset is the stride
+// between core matrices adjacent along K and the stride-byte offset the
+// stride between core matrices adjacent along M/N (measured on GB300 against
+// a host reference for both majors).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace csngf {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start address, leading-byte offset (K
+// direction), stride-byte offset (M/N direction), no swizzle
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                 // descriptor version of the sm_100 family
+  return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, A and B both BF16
+// (bf16 = true) or both FP16, A K-major (a_mn = 0) or MN-major (1), the same
+// for B, shape M x N
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int a_mn, int b_mn, int M, int N) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)a_mn << 15) |
+         ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// tensor memory: allocated by one whole warp; the base address lands in *slot
+__device__ __forceinline__ void alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               ::"r"(smem_addr(slot)), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory writes of the generic proxy (st.shared, cp.async) made visible
+// to the tensor core's reads of its operands
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem desc] * B[smem desc]; issued by one thread
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        bool accumulate) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)accumulate) : "memory");
+}
+// arrive once on the mbarrier when every MMA this thread issued so far is done
+__device__ __forceinline__ void commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 lanes (lane i of the warp's
+// quarter reads row i); complete after wait_ld()
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+               "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                 "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- mbarriers
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for the phase with the given parity to complete, for at most limit_ns;
+// false if it did not
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, unsigned long long limit_ns) {
+  const uint32_t a = smem_addr(mbar);
+  uint32_t done = 0;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+}  // namespace tc
+}  // namespace csngf

@@ -67,7 +67,12 @@ def test_prepare_rejects_bad_arguments_before_touching_the_device(binding):
     lib.cs_ngf_default_config(ctypes.byref(cfg))
     assert cfg.eps == pytest.approx(1e-5) and cfg.gamma == 0.5
     assert cfg.pad_mode == binding.PAD_MODES["bound"]      # bound-limited padding by default
-    assert ctypes.sizeof(binding.Config) == 40 and ctypes.sizeof(binding.Info) == 80
+    assert ctypes.sizeof(binding.Config) == 44 and ctypes.sizeof(binding.Info) == 80
+    assert cfg.tensor_cores == 1                            # tensor-core z pass by default
+    cfg.tensor_cores = 2
+    assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None, ctypes.byref(h)) == binding.EINVAL
+    assert b"tensor_cores" in lib.cs_ngf_last_error()
+    cfg.tensor_cores = 1
     cfg.pad_mode = 5
     assert lib.cs_ngf_prepare_fixed(fake, fake, dims, ctypes.byref(cfg), None, ctypes.byref(h)) == binding.EINVAL
     assert b"pad_mode" in lib.cs_ngf_last_error()
