@@ -291,14 +291,14 @@ def l2_note(roofline_step, R, batch):
             f"({batch} rotations) exceed the 129 MB L2")
 
 
-def time_form(cs_ngf, A, MA, B, MB, quats, precision, args, fp32_value):
+def time_form(cs_ngf, A, MA, B, MB, quats, precision, args, fp32_value, tensor_cores=True):
     """One precision form on the headline workload: the same step, warm-up and
     timed steps (CUDA events on the launching stream) as the FP32 line, then
     one scoring call for the per-rotation results.  Returns (summary dict,
     (scores, shifts) as numpy)."""
     import torch
     g = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=precision, pad_mode=args.pad_mode,
-                             autotune=args.autotune == "on")
+                             autotune=args.autotune == "on", tensor_cores=tensor_cores)
 
     def step():
         g.update_fixed(A, MA)
@@ -320,8 +320,12 @@ def time_form(cs_ngf, A, MA, B, MB, quats, precision, args, fp32_value):
     out = (sc.cpu().numpy(), sh.cpu().numpy())
     summary = {"value": value, "unit": UNIT, "ms_per_step": ms / args.steps,
                "ratio_to_fp32": value / fp32_value, "steps": args.steps,
+               "tensor_cores": bool(tensor_cores),
                "storage": f"{precision} channel fields of the forward x and y passes; mask / overlap "
                           "path and everything after the spectral sum FP32",
+               "z_pass": ("forward z DFT of the channel fields as tcgen05 MMAs "
+                          f"({precision} operands, FP32 accumulation in tensor memory)") if tensor_cores
+                         else "CUDA-core FFT (FP32 arithmetic)",
                "result": {"best_rotation": res[1], "shift": list(res[2]), "score": res[0]}}
     g.release()
     return summary, out
@@ -531,6 +535,9 @@ def run_ours(args):
         fs.start()
         for prec in ("bf16", "fp16"):
             forms[prec], form_results[prec] = time_form(cs_ngf, A, MA, B, MB, quats, prec, args, value)
+        # the same BF16 form with the z pass on the CUDA cores, for comparison
+        forms["bf16_cuda_cores"], _ = time_form(cs_ngf, A, MA, B, MB, quats, "bf16", args, value,
+                                                tensor_cores=False)
         fclk = fs.stop()
         for prec in forms:
             forms[prec]["clocks"] = fclk

@@ -136,12 +136,14 @@ typedef struct {
   int32_t tensor_cores; /* 1 (cs_ngf_default_config): in the BF16 and FP16 forms the z pass
                         runs the forward z-axis DFT of the NGF channel fields on the tensor
                         cores (BF16 / FP16 operands, FP32 accumulation; Eq. 7-8 unchanged)
-                        wherever the z length is at most 254 and has a split of at least
-                        8 columns (32, 40, 64, 80, 100, 128, 160, 200); the mask field and
-                        every inverse transform stay FP32 on the CUDA cores.  0: the CUDA-core
-                        FFT for every field.  Ignored in the FP32 form.  A tensor-core pass
-                        that waits more than 2 s for its own MMAs stops; the next synchronous
-                        call (cs_ngf_align, cs_ngf_score_rotations_host) then returns ECUDA. */
+                        wherever the z length is at most 200 (16 ... 200) and the block's
+                        operands fit in shared memory (at 200: z extent at most 160); the
+                        mask field and every inverse transform stay FP32 on the CUDA cores.
+                        The handle then holds one more per-rotation buffer (the spectral sum
+                        X, (Px/2+1) Py Pz complex values).  0: the CUDA-core FFT for every
+                        field.  Ignored in the FP32 form.  A tensor-core pass that waits more
+                        than 2 s for its own MMAs stops; the next synchronous call
+                        (cs_ngf_align, cs_ngf_score_rotations_host) then returns ECUDA. */
 } cs_ngf_config;
 
 typedef struct {

@@ -189,6 +189,7 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->thr);
   cudaFree(f->keys);
   cudaFree(f->tc_err);
+  cudaFree(f->zx);
   for (int a = 0; a < 3; ++a) {
     bool dup = false;
     for (int b = 0; b < a; ++b) dup |= (f->tw[b] == f->tw[a]);
@@ -848,13 +849,14 @@ cs_ngf_status resolve_pads_impl(const int32_t dims[3], const cs_ngf_config& cfg,
 
 struct Sizes {
   size_t f02_elems, f13_elems, fixed_f02, fixed_f13, per_rot, shared_ws, uv_elems;
+  size_t zx_elems;   // X of the tensor-core z pass per rotation (0 when it is not used)
 };
 
 // channel fields per measure: three packed pairs of Eq. 6 products, or two of
 // the Eq. 3 components; the mask field comes on top
 int channel_fields(int measure) { return measure == CS_NGF_UNSQUARED ? 2 : 3; }
 
-Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure, int precision) {
+Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure, int precision, int tensor_cores) {
   const size_t nz = dims[0], ny = dims[1], nx = dims[2];
   const size_t Pz = pad[0], Py = pad[1], Px = pad[2];
   const size_t vz = 2 * nz - 1, vy = 2 * ny - 1, nvox = nz * ny * nx;
@@ -866,7 +868,8 @@ Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure, int precis
   z.f13_elems = (std::max((nch * cb + 8) * E1, vz * vy * Px * 8) + 7) / 8;
   z.fixed_f02 = nf * E0;                                            // one rotation, FP32 (A side)
   z.fixed_f13 = nf * E1;
-  z.per_rot = (z.f02_elems + z.f13_elems) * sizeof(float2) + nvox * 5;
+  z.zx_elems = (tensor_cores && precision != CS_NGF_FP32) ? (Px / 2 + 1) * Py * Pz : 0;
+  z.per_rot = (z.f02_elems + z.f13_elems + z.zx_elems) * sizeof(float2) + nvox * 5;
   z.shared_ws = nvox * (sizeof(float2) + 1);                       // BP, C8
   z.uv_elems = (2 * nch + 1) * (Px / 2 + 1) * Py * Pz;
   return z;
@@ -910,8 +913,9 @@ cs_ngf_status set_lengths(cs_ngf_fixed* f, const int pad[3], cudaStream_t st) {
 cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]) {
   return ::resolve_pads_impl(dims, cfg, pad);
 }
-size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision) {
-  const Sizes z = ::sizes_for(dims, pad, measure, precision);
+size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision,
+                    int tensor_cores) {
+  const Sizes z = ::sizes_for(dims, pad, measure, precision, tensor_cores);
   size_t tw = 0;
   for (int a = 0; a < 3; ++a) tw += (size_t)pad[a] * sizeof(float2);
   const size_t nmarg = (size_t)dims[0] + dims[1] + dims[2];
@@ -988,7 +992,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   f->autotune = cfg.autotune;
   resolve_variants(f);
 
-  const Sizes sz = sizes_for(dims, pad, cfg.measure, cfg.precision);
+  const Sizes sz = sizes_for(dims, pad, cfg.measure, cfg.precision, cfg.tensor_cores);
   f->f02_elems = sz.f02_elems;
   f->f13_elems = sz.f13_elems;
   const size_t per_rot = sz.per_rot, shared_ws = sz.shared_ws, uv_elems = sz.uv_elems;
@@ -1027,6 +1031,10 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->bounds, (size_t)batch * 6));
   CS_TRYC(dalloc(&f->thr, (size_t)batch));
   CS_TRYC(dalloc(&f->keys, (size_t)batch));
+  if (sz.zx_elems) {
+    CS_TRYC(dalloc(&f->zx, (size_t)batch * sz.zx_elems));
+    g.zx = f->zx;
+  }
   CS_TRYC(dalloc(&f->tc_err, (size_t)1));
   CS_TRYC(cudaMemsetAsync(f->tc_err, 0, sizeof(int), st));
   g.tc_err = f->tc_err;

@@ -60,6 +60,7 @@ struct cs_ngf_fixed {
   float* thr = nullptr;
   unsigned long long* keys = nullptr;
   int* tc_err = nullptr;       // set by a tensor-core pass that stopped on its bounded wait
+  float2* zx = nullptr;        // X of the tensor-core z pass (reduced-precision forms), per launch group
   float2* tw[3] = {nullptr, nullptr, nullptr};   // z, y, x
   // rotation matrices: pinned host staging + device copy, grown on demand
   RotMat* rot_h = nullptr;
@@ -114,7 +115,8 @@ cs_ngf_status score_range(cs_ngf_fixed* f, int r0, int n, float* best_score, int
 // validate dims / cfg and return the FFT lengths; EINVAL / EUNSUPPORTED on error
 cs_ngf_status resolve_pads(const int32_t dims[3], const cs_ngf_config& cfg, int pad[3]);
 // device bytes a handle of these dims, FFT lengths and batch allocates
-size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision);
+size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision,
+                    int tensor_cores);
 
 }  // namespace detail
 }  // namespace csngf

@@ -52,6 +52,10 @@ struct Geo {
   // set to 1 by a tensor-core pass whose bounded wait for its own MMAs ran out
   // (it then stops and returns); nullptr: not reported
   int* tc_err;
+  // X of the tensor-core z pass, [r][kx <= Px/2][ky][kz] per launch group
+  // (the handle allocates it with the tensor-core forms); nullptr: the z pass
+  // runs as one kernel
+  float2* zx;
 };
 
 constexpr int kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2;

@@ -693,8 +693,8 @@ void launch_zmac(const void* F1, const float2* UV, float2* F2, const float2* tw,
       bool done = false;
       by_store(g.store, [&](auto sf) {
         constexpr int ST = decltype(sf)::value;
-        done = half ? launch_zmac_tc_t<P, ST, true, V>(F1, UV, F2, tw, g, nrot, bounds, st)
-                    : launch_zmac_tc_t<P, ST, false, V>(F1, UV, F2, tw, g, nrot, bounds, st);
+        done = half ? launch_zsplit_t<P, ST, true, V>(F1, UV, F2, tw, g, nrot, bounds, st)
+                    : launch_zsplit_t<P, ST, false, V>(F1, UV, F2, tw, g, nrot, bounds, st);
       });
       if (done) return;
     }

@@ -52,6 +52,7 @@ struct Slot {                     // device resources of one volume shape
   int measure;
   int precision;
   int pad_mode;
+  int tensor_cores;
   cs_ngf_fixed* f = nullptr;
   float* dA = nullptr;
   uint8_t* dMA = nullptr;
@@ -122,16 +123,18 @@ struct cs_ngf_server {
 namespace {
 
 size_t slot_bytes(const int32_t dims[3], const int pad[3], int batch, int measure, int precision,
-                  int cap) {
+                  int tensor_cores, int cap) {
   const size_t nvox = (size_t)dims[0] * dims[1] * dims[2];
-  return csngf::detail::handle_bytes(dims, pad, batch, measure, precision) + nvox * 10 + (size_t)cap * 16;
+  return csngf::detail::handle_bytes(dims, pad, batch, measure, precision, tensor_cores) + nvox * 10 +
+         (size_t)cap * 16;
 }
 
 bool same_shape(const Slot& s, const Job& j) {
   return std::memcmp(s.dims, j.dims, sizeof(s.dims)) == 0 &&
          std::memcmp(s.pad, j.pad, sizeof(s.pad)) == 0 && s.eps == j.cfg.eps &&
          s.gamma == j.cfg.gamma && s.batch == j.cfg.batch && s.measure == j.cfg.measure &&
-         s.precision == j.cfg.precision && s.pad_mode == j.cfg.pad_mode;
+         s.precision == j.cfg.precision && s.pad_mode == j.cfg.pad_mode &&
+         s.tensor_cores == j.cfg.tensor_cores;
 }
 
 void free_slot(Slot* s) {
@@ -257,6 +260,7 @@ Slot* find_slot(cs_ngf_server* sv, Job* j, bool* fresh) {
   s->measure = j->cfg.measure;
   s->precision = j->cfg.precision;
   s->pad_mode = j->cfg.pad_mode;
+  s->tensor_cores = j->cfg.tensor_cores;
   s->bytes = need;
   sv->bytes_in_use += need;
   sv->slots.push_back(std::move(s));
@@ -488,7 +492,8 @@ cs_ngf_status cs_ngf_server_submit(cs_ngf_server* sv, const float* A, const uint
   std::memcpy(j->dims, dims, sizeof(j->dims));
   j->R = R;
   j->est_ms = (double)R * j->pad[0] * j->pad[1] * j->pad[2] * 2.5e-8;
-  j->bytes = slot_bytes(dims, j->pad, j->cfg.batch, j->cfg.measure, j->cfg.precision, R);
+  j->bytes = slot_bytes(dims, j->pad, j->cfg.batch, j->cfg.measure, j->cfg.precision,
+                        j->cfg.tensor_cores, R);
   if (j->bytes > (size_t)sv->cfg.memory_budget_bytes)
     return fail(CS_NGF_ENOMEM, "job needs " + std::to_string(j->bytes) + " device bytes, budget is " +
                                    std::to_string(sv->cfg.memory_budget_bytes));

@@ -1,7 +1,8 @@
-"""The tensor-core z pass of the reduced-precision forms (k_zmac_tc: the
+"""The tensor-core z pass of the reduced-precision forms (k_zx_tc: the
 forward z-axis DFT of the channel fields as BF16 / FP16 MMAs with FP32
-accumulation in tensor memory) against the FP64 oracle, element by element,
-at every z length it runs at, through the C ABI.
+accumulation in tensor memory, and the Eq. 7-8 sum; k_zinv: the FP32 mask
+field and the inverse) against the FP64 oracle, element by element, at every
+z length it runs at, through the C ABI.
 
 Each case also scores the same input with the CUDA-core FFT of the same
 precision form (tensor_cores=False): the two maps must differ (so the
@@ -70,12 +71,13 @@ def run_case(cs, p, pad, pad_mode, precision="bf16", measure="squared", autotune
 # every z length the tensor-core pass takes, half-length inputs (n <= P/2),
 # full padding with the lengths given
 TC_LENGTH_CASES = [
-    ((12, 10, 14), (32, 32, 32)),        # 4 x 8 split: 4 warps, one per tensor-memory lane quarter
-    ((18, 12, 9), (40, 32, 32)),         # 4 x 10: 5 warps
+    ((7, 10, 6), (16, 32, 16)),          # 4 x 4 split: the CUDA-core half has 2 warps
+    ((12, 10, 14), (32, 32, 32)),
+    ((18, 12, 9), (40, 32, 32)),
     ((30, 10, 12), (64, 32, 32)),
     ((36, 9, 11), (80, 32, 32)),
     ((45, 10, 9), (100, 100, 32)),       # ragged y tail: 100 columns in blocks of 8
-    ((60, 8, 10), (128, 16, 32)),        # 8 x 16: 8 warps, two per lane quarter
+    ((60, 8, 10), (128, 16, 32)),
     ((70, 9, 8), (160, 32, 16)),
     ((90, 8, 9), (200, 16, 32)),         # the 150^3 workload's z length
 ]
@@ -91,8 +93,8 @@ def test_tensor_core_z_pass_every_length(cs, dims, pad):
                                       ((90, 8, 9), (200, 16, 32))])
 def test_tensor_core_z_pass_alternative_splits(cs, dims, pad):
     """The second radix split of each length (4 x 16, 4 x 32, 8 x 25) changes
-    the block's thread count (256, 512, 400 with a half warp): the same MMA
-    and multiply-accumulate mapping must hold."""
+    the CUDA-core half's block (256, 512 and 400 threads, the last with a
+    half warp)."""
     p = synth.small_pair(950 + sum(dims), dims, masks="threshold", n_rot=3)
     run_case(cs, p, pad, "full", autotune="alternative", expect_pz=pad[0])
 
