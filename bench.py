@@ -200,7 +200,8 @@ def kernel_source_hash():
     left out: they launch the same kernels)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_10156_gb300", "csrc")
-    keep = ("fft_core.cuh", "kernels.cuh", "passes.cuh", "elem.cu", "cs_ngf.cu", "handle.h")
+    keep = ("fft_core.cuh", "kernels.cuh", "passes.cuh", "elem.cu", "cs_ngf.cu", "handle.h",
+            "tc.cuh", "zmac_tc.cuh")
     for fn in sorted(os.listdir(csrc)):
         if fn in keep or (fn.startswith("passes_") and fn.endswith(".cu")):
             with open(os.path.join(csrc, fn), "rb") as fh:

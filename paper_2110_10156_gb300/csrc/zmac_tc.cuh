@@ -63,12 +63,13 @@ constexpr unsigned long long kTcWaitNs = 2000000000ull;
 // rotation of the launch; the cos / sin tiles and the block's U_j, V_j stay
 // in shared memory.  Rotation r + 1's MMAs run while rotation r's products
 // are summed; rotation r + 2's operand is copied (cp.async) as soon as
-// rotation r's MMAs are done.  8 warps, two per tensor-memory lane quarter.
+// rotation r's MMAs are done.  16 warps, four per tensor-memory lane quarter.
 // ---------------------------------------------------------------------------
 template <int P>
 struct ZxTcCfg {
   static constexpr int W = 8;                          // primary columns per block
-  static constexpr int NT = 256;                       // 8 warps: 2 per tensor-memory lane quarter
+  static constexpr int NT = 512;                       // 16 warps: 4 per tensor-memory lane quarter,
+                                                       // each summing two primary columns
   static constexpr int HF = P / 2;
   static constexpr bool OK = HF + 1 <= 128;
   static constexpr uint32_t TMEM_COLS = 512;           // 2 buffers x (C, S) x N <= 512 columns
@@ -189,7 +190,7 @@ k_zx_tc(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __re
   bool failed = false;
   int fail_buf = 0;
   uint32_t fail_par = 0;
-  const int lq = warp & 3, cg = warp >> 2;         // lane quarter, column half
+  const int lq = warp & 3, cg = warp >> 2;         // lane quarter, column pair
   const int kz = lq * 32 + lane;
   const bool kz_ok = kz <= HF;
   const int kzm = kz == 0 ? 0 : P - kz;
@@ -218,8 +219,8 @@ k_zx_tc(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __re
     // (3) Eq. 7-8: X at kz and P - kz of this thread's four primary columns
     const uint32_t trow = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(s * 2 * NB);
     float2* Xr = Xg + (((long long)r * hx + kx) * g.Py + ky0) * P;
-#pragma unroll 1
-    for (int ch = cg; ch < 4; ch += 2) {           // two primary columns per step
+    {
+      const int ch = cg;                           // primary columns 2 ch, 2 ch + 1
       uint32_t rc[3][4], rs[3][4], rcm[3][4], rsm[3][4];
 #pragma unroll
       for (int j = 0; j < 3; ++j)

@@ -1,11 +1,13 @@
 """Small, self-contained workload for kernel profiling (ncu) of the scoring path.
 
     python -m paper_2110_10156_gb300.profile_workload --size 150 --rotations 2 --batch 2
+    python -m paper_2110_10156_gb300.profile_workload --headline 0 --rotations 4 --batch 4
 
 Builds a seeded synthetic pair of the given cube size (the 150^3 generator
-recipe scaled), prepares the fixed spectra and scores the requested number of
-rotations once, so that a profiler sees one launch of every kernel per batch
-with only a few GB held on the device.
+recipe scaled), or takes the 150^3 workload's own pair and a slice of its
+rotations (--headline), prepares the fixed spectra and scores the rotations
+once, so that a profiler sees one launch of every kernel per batch with only
+a few GB held on the device.
 """
 from __future__ import annotations
 
@@ -76,6 +78,9 @@ def main(argv=None) -> int:
     ap.add_argument("--rotations", type=int, default=2)
     ap.add_argument("--batch", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--headline", type=int, default=-1, metavar="FIRST",
+                    help="score the 150^3 workload's own pair, rotations FIRST .. FIRST + rotations - 1")
+    ap.add_argument("--tensor-cores", choices=("on", "off"), default="on")
     args = ap.parse_args(argv)
     if args.traffic_from:
         import json
@@ -91,17 +96,22 @@ def main(argv=None) -> int:
 
     from . import cs_ngf, synth
     n = args.size
-    p = synth.make_pair(1001, (n, n, n), max(4, int(40 * n / 150)), max(2.0, 5 * n / 150),
-                        max(3.0, 30 * n / 150), 30.0, max(1, int(20 * n / 150)),
-                        args.rotations, masks="threshold")
+    if args.headline >= 0:
+        p = synth.config_pair(1)
+        quats = p.quats[args.headline:args.headline + args.rotations]
+    else:
+        p = synth.make_pair(1001, (n, n, n), max(4, int(40 * n / 150)), max(2.0, 5 * n / 150),
+                            max(3.0, 30 * n / 150), 30.0, max(1, int(20 * n / 150)),
+                            args.rotations, masks="threshold")
+        quats = p.quats
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     f = cs_ngf.prepare_fixed(dev(p.A), dev(p.MA), batch=args.batch, precision=args.precision,
-                             pad_mode=args.pad_mode)
+                             pad_mode=args.pad_mode, tensor_cores=args.tensor_cores == "on")
     B, MB = dev(p.B), dev(p.MB)
     for _ in range(args.repeat):
-        sc, sh = f.score_rotations(B, MB, p.quats)
+        sc, sh = f.score_rotations(B, MB, quats)
     torch.cuda.synchronize()
-    print(f"dims {p.A.shape} pad {f.pad} batch {f.batch} best {float(sc.max()):.6f}")
+    print(f"dims {p.A.shape} classes {f.length_classes()} batch {f.batch} best {float(sc.max()):.6f}")
     f.release()
     return 0
 
