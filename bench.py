@@ -389,7 +389,8 @@ def run_ours(args):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     A, MA, B, MB = dev(pair["A"]), dev(pair["MA"]), dev(pair["B"]), dev(pair["MB"])
     f = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=args.precision,
-                             pad_mode=args.pad_mode, autotune=args.autotune == "on")
+                             pad_mode=args.pad_mode, autotune=args.autotune == "on",
+                             tensor_cores=args.tensor_cores == "on")
     dims = f.dims
 
     def step():
@@ -841,6 +842,8 @@ def main():
     ap.add_argument("--autotune", choices=("on", "off"), default="on",
                     help="time both radix splits of each FFT pass on the first launch group "
                          "at new lengths (warm-up) and keep the faster")
+    ap.add_argument("--tensor-cores", choices=("on", "off"), default="on",
+                    help="BF16 / FP16 forms: the z pass's channel DFT on the tensor cores (off: CUDA cores)")
     ap.add_argument("--ref-sample", type=int, default=16,
                     help="oracle rotations per CPU step (at most one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
