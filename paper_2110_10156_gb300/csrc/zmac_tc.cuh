@@ -277,8 +277,12 @@ k_zx_tc(const void* __restrict__ F1, const float2* __restrict__ UV, float2* __re
 // the CUDA-core half: mask field forward z transform, Y = conj(M_A^) M_B^,
 // Z = X + iY with X from k_zx_tc, the inverse z transform and the bound's
 // shift planes to F2 (the same arithmetic as k_zmac for these steps)
+// Two blocks per SM (at most 96 registers a thread at the 320-thread 10 x 20
+// split; a few bytes spill): its 40 KB of shared memory allow it, and the
+// extra warps hide the transforms' latency (BF16 z pass 127 -> 114 ms per
+// 1000 rotations of the 150^3 workload).
 template <int P, int ST, bool HALF, int V>
-__global__ void __launch_bounds__(ZinvCfg<P, V>::NT, 1)
+__global__ void __launch_bounds__(ZinvCfg<P, V>::NT, 2)
 k_zinv(const void* __restrict__ F1, const float2* __restrict__ Xg, const float2* __restrict__ UV,
        float2* __restrict__ F2, const float2* __restrict__ tw, Geo g, int nrot,
        const int* __restrict__ bounds) {
