@@ -17,6 +17,10 @@
 #include <stdint.h>
 
 namespace csngf {
+
+// wait limit of a tensor-core pass for its own MMAs (they take microseconds)
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
+
 namespace tc {
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

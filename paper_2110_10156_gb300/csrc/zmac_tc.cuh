@@ -48,9 +48,6 @@ __device__ __forceinline__ void store16(unsigned char* p, float v) {
   else *reinterpret_cast<__half*>(p) = __float2half_rn(v);
 }
 
-// wait limit of the tensor-core pass for its own MMAs (they take microseconds)
-constexpr unsigned long long kTcWaitNs = 2000000000ull;
-
 // ---------------------------------------------------------------------------
 // k_zx_tc forms X, the Eq. 7-8 sum of the weighted channel products, for
 // every column of the half spectrum kx <= P/2, in HBM; k_zinv reads it.  X
