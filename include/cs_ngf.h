@@ -17,11 +17,19 @@
  *
  * Conventions (the paper leaves these open; the library fixes them):
  *   - Volumes are [z][y][x] with x contiguous; dims[] = {nz, ny, nx}, each in
- *     [2, 256].  B has the same dims as A.
+ *     [2, 256].  B has the same dims as A.  The cap comes from the longest
+ *     FFT length built, 512 >= 2n - 1 (a rotation whose admitted shifts span
+ *     the whole range needs the full linear length).  Volumes up to 512 per
+ *     axis would need 1024-point transforms, which are not built (their fixed
+ *     spectra take about 30 GB, each rotation's fields about 15 GB); at 1024
+ *     per axis the 2048-point fixed spectra alone (about 240 GB) leave no room
+ *     for a rotation in HBM.
  *   - Vectors are (x, y, z).  Rotation centre c = (n - 1) / 2 per axis and
  *     B_hat(x) = B(R(q)(x - c) + c), R the Hamilton matrix of the unit
  *     quaternion q = (w, x, y, z), built in FP64 on the host with entries
- *     within 1e-9 of -1, 0, 1 snapped, then rounded to FP32.
+ *     within 1e-9 of -1, 0, 1 snapped, then rounded to FP32.  Quaternions
+ *     are therefore HOST float64 arrays, not device floats: the matrix is
+ *     formed once per rotation on the host and uploaded with the batch.
  *   - The rotated mask is [trilinear M_B >= 0.5] at sample points inside
  *     [0, n-1]^3 (1e-4 slack); outside, B_hat = 0 and the mask is 0.
  *   - Gradient: central differences, unit spacing, indices clamped at faces.
@@ -42,7 +50,12 @@
  * cudaStream_t, NULL = legacy default stream); the caller keeps the inputs
  * alive until that work completes.  A handle owns all of its device memory
  * (fixed spectra and per-batch workspace) and is used by one host thread at
- * a time.  No function aborts the process: each returns a status.
+ * a time: a call that finds another thread inside a call on the same handle
+ * returns CS_NGF_EBUSY at once, without touching the handle.  Calls on one
+ * handle may use different streams: each call's work waits for the previous
+ * call's (an event recorded on the previous call's stream), so they never
+ * overlap on the handle's buffers.  No function aborts the process: each
+ * returns a status.
  */
 #ifndef CS_NGF_H
 #define CS_NGF_H
@@ -63,7 +76,8 @@ typedef enum {
   CS_NGF_ENOVALID = 4,    /* no rotation had any valid shift */
   CS_NGF_EUNSUPPORTED = 5, /* FFT length or size not supported */
   CS_NGF_ECANCELED = 6,    /* a served job was cancelled */
-  CS_NGF_ETIMEOUT = 7      /* a wait ended before the job finished */
+  CS_NGF_ETIMEOUT = 7,     /* a wait ended before the job finished */
+  CS_NGF_EBUSY = 8         /* another host thread is inside a call on this handle */
 } cs_ngf_status;
 
 typedef enum {
@@ -187,7 +201,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
  * Asynchronous on `stream` except for the small host-to-device upload of the
  * rotation matrices, which is staged through the handle, and, with
  * bound-limited padding, one wait for the shift range of the call (the call
- * returns once the scoring work is enqueued).  Errors: EINVAL, ECUDA. */
+ * returns once the scoring work is enqueued).  Errors: EINVAL, EBUSY, ECUDA. */
 cs_ngf_status cs_ngf_score_rotations(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
                                      const double* quats, int32_t R, float* best_score,
                                      int32_t* best_shift, void* stream);
@@ -195,32 +209,33 @@ cs_ngf_status cs_ngf_score_rotations(cs_ngf_fixed* f, const float* B, const uint
 /* cs_ngf_score_rotations with HOST buffers: copies B and maskB (host,
  * [nz][ny][nx]) to the handle's device staging area, scores, and copies the
  * results back to host best_score [R] / best_shift [R][3].  Synchronous.
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * Errors: EINVAL, EBUSY, ENOMEM, ECUDA. */
 cs_ngf_status cs_ngf_score_rotations_host(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
                                           const double* quats, int32_t R, float* best_score,
                                           int32_t* best_shift, void* stream);
 
 /* Fig. 1: the maximum of s_ANGF over all rotations and shifts.
  *   score, rot_index, shift: HOST outputs (score -inf, index -1 if nothing
- *   is valid, with status ENOVALID).  Synchronous.  B, maskB device. */
+ *   is valid, with status ENOVALID).  Synchronous.  B, maskB device.
+ * Errors: EINVAL, EBUSY, ENOVALID, ENOMEM, ECUDA. */
 cs_ngf_status cs_ngf_align(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
                            const double* quats, int32_t R, float* score, int32_t* rot_index,
                            int32_t shift[3], void* stream);
 
 /* Eq. 5 for one rotation, the full map: map is device float32
  * [2nz-1][2ny-1][2nx-1] indexed by chi + n - 1, holding CSNGF(chi) or -inf
- * where chi is not valid.  quat: host float64 [4].  Errors: EINVAL, ECUDA. */
+ * where chi is not valid.  quat: host float64 [4].  Errors: EINVAL, EBUSY, ECUDA. */
 cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
                                const double* quat, float* map, void* stream);
 
 /* Section 3.2 resample alone (one rotation): B_hat device float32 and M_hat
- * device uint8, [nz][ny][nx].  quat: host float64 [4]. */
+ * device uint8, [nz][ny][nx].  quat: host float64 [4].  Errors: EINVAL, EBUSY, ECUDA. */
 cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
                               const double* quat, float* Bhat, uint8_t* Mhat, void* stream);
 
 /* Recompute the fixed-volume spectra of an existing handle from a new A and
  * maskA of the same dims (no reallocation).  Synchronises `stream`.
- * Errors: EINVAL, ECUDA. */
+ * Errors: EINVAL, EBUSY, ECUDA. */
 cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t* maskA,
                                   void* stream);
 
@@ -228,7 +243,7 @@ cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t
  * is bracketed by CUDA events recorded on its stream.  cs_ngf_stage_times
  * waits for them and returns, per stage, the summed milliseconds and the
  * number of launches since the previous call (host arrays of
- * CS_NGF_NSTAGES), then forgets them.  Stages: */
+ * CS_NGF_NSTAGES), then forgets them.  Errors: EINVAL, EBUSY, ECUDA.  Stages: */
 #define CS_NGF_NSTAGES 8
 enum {
   CS_NGF_STAGE_RESAMPLE = 0, /* Section 3.2 trilinear resample + rotated mask */

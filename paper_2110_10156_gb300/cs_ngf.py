@@ -21,7 +21,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-OK, EINVAL, ENOMEM, ECUDA, ENOVALID, EUNSUPPORTED, ECANCELED, ETIMEOUT = range(8)
+OK, EINVAL, ENOMEM, ECUDA, ENOVALID, EUNSUPPORTED, ECANCELED, ETIMEOUT, EBUSY = range(9)
 
 EXPORTED = (
     "cs_ngf_default_config", "cs_ngf_prepare_fixed", "cs_ngf_score_rotations",

@@ -196,6 +196,7 @@ void free_handle(cs_ngf_fixed* f) {
     if (!dup) cudaFree(f->tw[a]);
   }
   if (f->rot_ev) cudaEventSynchronize(f->rot_ev);
+  if (f->order_ev) cudaEventDestroy(f->order_ev);
   for (auto& sp : f->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
   if (f->gexec) cudaGraphExecDestroy(f->gexec);
   for (auto& gs : f->graphs) cudaGraphExecDestroy(gs.exec);
@@ -928,6 +929,39 @@ size_t handle_bytes(const int32_t dims[3], const int pad[3], int batch, int meas
 }  // namespace csngf
 
 // ============================================================================
+namespace {
+// A call on a handle: claims it for this host thread (a second thread gets
+// EBUSY and leaves the handle alone) and, with `order`, makes `st` wait for
+// the event the previous call recorded on its own stream; on leaving, the
+// call records that event on `st`.  Work of successive calls therefore never
+// overlaps on the handle's buffers, whatever streams the calls use.
+struct HandleCall {
+  cs_ngf_fixed* f;
+  cudaStream_t st;
+  bool order;
+  bool held = false;
+  cudaError_t err = cudaSuccess;
+  HandleCall(cs_ngf_fixed* h, cudaStream_t s, bool ord) : f(h), st(s), order(ord) {
+    int idle = 0;
+    held = f->busy.compare_exchange_strong(idle, 1, std::memory_order_acquire);
+    if (held && order && f->order_ev) err = cudaStreamWaitEvent(st, f->order_ev, 0);
+  }
+  ~HandleCall() {
+    if (!held) return;
+    if (order && f->order_ev) cudaEventRecord(f->order_ev, st);
+    f->busy.store(0, std::memory_order_release);
+  }
+};
+}  // namespace
+
+// claim handle f for this call (after its device is current); returns EBUSY
+// or ECUDA from the calling function
+#define CS_CLAIM(f, st, order)                                                         \
+  HandleCall call_((f), (st), (order));                                                \
+  if (!call_.held) return fail(CS_NGF_EBUSY, "another host thread is inside a call on this handle"); \
+  if (call_.err != cudaSuccess)                                                        \
+    return fail(CS_NGF_ECUDA, std::string("cudaStreamWaitEvent: ") + cudaGetErrorString(call_.err))
+
 extern "C" {
 
 static_assert(sizeof(cs_ngf_config) == 44, "cs_ngf_config layout (the Python binding mirrors it)");
@@ -953,6 +987,7 @@ const char* cs_ngf_status_string(int32_t s) {
     case CS_NGF_EUNSUPPORTED: return "unsupported size";
     case CS_NGF_ECANCELED: return "cancelled";
     case CS_NGF_ETIMEOUT: return "timed out";
+    case CS_NGF_EBUSY: return "handle busy";
     default: return "unknown status";
   }
 }
@@ -1035,6 +1070,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
     CS_TRYC(dalloc(&f->zx, (size_t)batch * sz.zx_elems));
     g.zx = f->zx;
   }
+  CS_TRYC(cudaEventCreateWithFlags(&f->order_ev, cudaEventDisableTiming));
   CS_TRYC(dalloc(&f->tc_err, (size_t)1));
   CS_TRYC(cudaMemsetAsync(f->tc_err, 0, sizeof(int), st));
   g.tc_err = f->tc_err;
@@ -1054,6 +1090,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
 
   // A side into the new handle
   CS_TRY(run_fixed(f, A, maskA, st));
+  CS_TRYC(cudaEventRecord(f->order_ev, st));
 #undef CS_TRY
 #undef CS_TRYC
   *out = f;
@@ -1066,7 +1103,9 @@ cs_ngf_status cs_ngf_score_rotations(cs_ngf_fixed* f, const float* B, const uint
   g_last_error.clear();
   if (cs_ngf_status s = check_volume_args(f, B, maskB)) return s;
   DeviceGuard guard(f->device);
-  return score_all(f, B, maskB, quats, R, best_score, best_shift, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  CS_CLAIM(f, st, true);
+  return score_all(f, B, maskB, quats, R, best_score, best_shift, st);
 }
 
 cs_ngf_status cs_ngf_score_rotations_host(cs_ngf_fixed* f, const float* B, const uint8_t* maskB,
@@ -1078,6 +1117,7 @@ cs_ngf_status cs_ngf_score_rotations_host(cs_ngf_fixed* f, const float* B, const
   if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
   DeviceGuard guard(f->device);
   cudaStream_t st = (cudaStream_t)stream;
+  CS_CLAIM(f, st, true);
   if (!f->stage_B) {
     CS_CUDA(dalloc(&f->stage_B, (size_t)f->g.nvox));
     CS_CUDA(dalloc(&f->stage_M, (size_t)f->g.nvox));
@@ -1102,6 +1142,7 @@ cs_ngf_status cs_ngf_align(cs_ngf_fixed* f, const float* B, const uint8_t* maskB
   if (R <= 0) return fail(CS_NGF_EINVAL, "R must be positive");
   DeviceGuard guard(f->device);
   cudaStream_t st = (cudaStream_t)stream;
+  CS_CLAIM(f, st, true);
   if (cs_ngf_status s = ensure_results(f, R)) return s;
   if (cs_ngf_status s = score_all(f, B, maskB, quats, R, f->res_score, f->res_shift, st)) return s;
   std::vector<float> sc(R);
@@ -1132,6 +1173,7 @@ cs_ngf_status cs_ngf_score_map(cs_ngf_fixed* f, const float* B, const uint8_t* m
   if (!map) return fail(CS_NGF_EINVAL, "map is NULL");
   DeviceGuard guard(f->device);
   cudaStream_t st = (cudaStream_t)stream;
+  CS_CLAIM(f, st, true);
   if (cs_ngf_status s = ensure_results(f, 1)) return s;
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
   if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
@@ -1148,6 +1190,7 @@ cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* ma
   if (!Bhat || !Mhat) return fail(CS_NGF_EINVAL, "output pointer is NULL");
   DeviceGuard guard(f->device);
   cudaStream_t st = (cudaStream_t)stream;
+  CS_CLAIM(f, st, true);
   if (cs_ngf_status s = upload_rotations(f, quat, 1, st)) return s;
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
   const Geo& g = f->g;
@@ -1239,6 +1282,7 @@ cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t
   if (!A || !maskA) return fail(CS_NGF_EINVAL, "A or maskA is NULL");
   DeviceGuard guard(f->device);
   cudaStream_t st = (cudaStream_t)stream;
+  CS_CLAIM(f, st, true);
   if (f->A_keep) {                               // kept for later changes of FFT length
     CS_CUDA(cudaMemcpyAsync(f->A_keep, A, sizeof(float) * f->g.nvox, cudaMemcpyDeviceToDevice, st));
     CS_CUDA(cudaMemcpyAsync(f->MA_keep, maskA, (size_t)f->g.nvox, cudaMemcpyDeviceToDevice, st));
@@ -1248,6 +1292,7 @@ cs_ngf_status cs_ngf_update_fixed(cs_ngf_fixed* f, const float* A, const uint8_t
 
 cs_ngf_status cs_ngf_set_profiling(cs_ngf_fixed* f, int32_t on) {
   if (!f) return fail(CS_NGF_EINVAL, "handle is NULL");
+  CS_CLAIM(f, nullptr, false);
   f->profiling = on != 0;
   return CS_NGF_OK;
 }
@@ -1255,6 +1300,7 @@ cs_ngf_status cs_ngf_set_profiling(cs_ngf_fixed* f, int32_t on) {
 cs_ngf_status cs_ngf_stage_times(cs_ngf_fixed* f, double* ms, int64_t* launches) {
   if (!f || !ms || !launches) return fail(CS_NGF_EINVAL, "NULL argument");
   DeviceGuard guard(f->device);
+  CS_CLAIM(f, nullptr, false);
   for (int i = 0; i < CS_NGF_NSTAGES; ++i) { ms[i] = 0.0; launches[i] = 0; }
   cs_ngf_status st = CS_NGF_OK;
   for (auto& sp : f->spans) {

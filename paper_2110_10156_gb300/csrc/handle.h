@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -85,6 +86,13 @@ struct cs_ngf_fixed {
   bool profiling = false;
   struct Span { int stage; cudaEvent_t a, b; };
   std::vector<Span> spans;
+  // one call at a time: set while a host thread is inside a call on this
+  // handle (a second thread gets CS_NGF_EBUSY)
+  std::atomic<int> busy{0};
+  // recorded on the caller's stream at the end of every call; the next call
+  // waits for it on its own stream, so calls on different streams do not
+  // overlap on the workspace
+  cudaEvent_t order_ev = nullptr;
 };
 
 namespace csngf {

@@ -49,7 +49,17 @@ def test_status_strings(binding):
     lib = binding.library()
     assert lib.cs_ngf_status_string(0) == b"ok"
     assert lib.cs_ngf_status_string(1) == b"invalid argument"
+    assert lib.cs_ngf_status_string(binding.EBUSY) == b"handle busy"
     assert lib.cs_ngf_status_string(99) == b"unknown status"
+
+
+def test_header_status_codes_match_the_binding(binding):
+    """Every CS_NGF_E* code of the header has the same value in the binding."""
+    text = open(HEADER).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"\bCS_NGF_(E[A-Z]+|OK) = (\d+)", text))
+    assert codes["EBUSY"] == 8
+    for name, value in codes.items():
+        assert getattr(binding, name) == value, name
 
 
 def test_prepare_rejects_bad_arguments_before_touching_the_device(binding):
