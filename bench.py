@@ -209,9 +209,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(stage: str, precision: str = "fp32"):
-    """DRAM bytes per rotation for a stage from the committed ncu summary, if it
-    was taken on the current kernel sources in the same precision; else None."""
+def ncu_traffic(stage: str, precision: str = "fp32", dims=None, pad=None):
+    """(DRAM bytes per rotation, DRAM bytes every launch moves whatever its
+    rotation count) for a stage at FFT lengths `pad`, from the committed ncu
+    summary, if it was taken on the current kernel sources in the same
+    precision; else None.  Lengths the summary has no capture of take the
+    captured class nearest in grid points, scaled by the byte model's ratio
+    between the two (per rotation: the launch's bytes at one rotation less the
+    per-launch tile; per launch: the fixed-spectra tile's size)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
@@ -220,8 +225,34 @@ def ncu_traffic(stage: str, precision: str = "fp32"):
         return None
     if d.get("src_hash") != kernel_source_hash() or d.get("precision", "fp32") != precision:
         return None
-    e = d.get("stages", {}).get(stage)
-    return None if e is None else float(e["dram_bytes_per_rotation"])
+    classes = [c for c in d.get("classes", []) if stage in c.get("stages", {})]
+    if not classes:
+        return None
+    exact = [c for c in classes if pad is not None and c.get("fft") == list(pad)]
+    if exact or pad is None or dims is None or any(c.get("fft") is None for c in classes):
+        e = (exact or classes)[0]["stages"][stage]
+        return float(e["dram_bytes_per_rotation"]), float(e.get("dram_bytes_per_launch_fixed", 0.0))
+    npts = lambda q: q[0] * q[1] * q[2]
+    c = min(classes, key=lambda c: abs(npts(c["fft"]) - npts(pad)))
+    e, cap = c["stages"][stage], tuple(c["fft"])
+    one = lambda q: stage_bytes(dims, q, 1, stage, precision=precision) - stage_bytes(dims, q, 0, stage, precision=precision)
+    tile = lambda q: stage_bytes(dims, q, 0, stage, precision=precision)
+    pr = float(e["dram_bytes_per_rotation"]) * (one(pad) / one(cap) if one(cap) else 1.0)
+    fx = float(e.get("dram_bytes_per_launch_fixed", 0.0)) * (tile(pad) / tile(cap) if tile(cap) else 1.0)
+    return pr, fx
+
+
+def launch_traffic(stage: str, precision: str, dims, launches_of):
+    """ncu DRAM bytes of a stage summed over the launches of one step, each
+    launch (lengths, rotations) at its own class's figures; None without a
+    current summary."""
+    tot = 0.0
+    for cp, nb in launches_of:
+        t = ncu_traffic(stage, precision, dims, cp)
+        if t is None:
+            return None
+        tot += t[1] + t[0] * nb
+    return tot
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -492,12 +523,11 @@ def run_ours(args):
     total_bytes = sum(stage_bytes(dims, cp, nb, dom, precision=args.precision) for cp, nb in launches_of)
     total_bytes *= prof_steps
     achieved = total_bytes / (stage_ms[dom] / 1000.0) / 1e9 if stage_ms[dom] > 0 else 0.0
-    tr = ncu_traffic(dom, args.precision)
-    per_launch_rot = R / nbatches
+    tr = launch_traffic(dom, args.precision, dims, launches_of)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel": dom,
-                "traffic": None if tr is None else tr * per_launch_rot,
+                "traffic": None if tr is None else tr / nbatches,
                 "algorithmic_bytes_per_launch": total_bytes / (prof_steps * nbatches),
                 "timing": "CUDA events around every launch of one profiled step after the timed region"}
     if dom == "zmac":               # the same without the F2 writes (a lower bound)
@@ -510,11 +540,11 @@ def run_ours(args):
     # the whole step against HBM: the ncu DRAM bytes per rotation of every
     # scoring stage (same kernel sources and precision only), times the
     # rotations, over the timed step
-    step_bytes = [ncu_traffic(st, args.precision) for st in ("resample", "fwd_x", "fwd_y", "zmac",
-                                                            "inv_y", "inv_x")]
+    step_bytes = [launch_traffic(st, args.precision, dims, launches_of)
+                  for st in ("resample", "fwd_x", "fwd_y", "zmac", "inv_y", "inv_x")]
     roofline_step = None
     if all(b is not None for b in step_bytes):
-        per_rot = sum(step_bytes)
+        per_rot = sum(step_bytes) / R
         ach = per_rot * R / (elapsed_ms / args.steps / 1000.0) / 1e9
         roofline_step = {"bound": "hbm", "dram_bytes_per_rotation": per_rot, "achieved": ach,
                          "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -642,13 +672,16 @@ def run_small_latency(args):
 
 
 def run_large(args):
-    """256^3 pair, 512^3 FFT: rotations/s in FP32 (memory-sized batches)."""
+    """256^3 pair (full linear length 512 per axis; bound-limited padding takes
+    400 or 320): rotations/s in the precision asked for (memory-sized
+    batches)."""
     import torch
     from paper_2110_10156_gb300 import cs_ngf
     R = args.rotations if args.rotations != 1000 else 5000
     pair = load_pair(4, R)
     A, MA, B, MB = (_dev(pair[k]) for k in ("A", "MA", "B", "MB"))
-    f = cs_ngf.prepare_fixed(A, MA, batch=args.batch)
+    f = cs_ngf.prepare_fixed(A, MA, batch=args.batch, precision=args.precision,
+                             pad_mode=args.pad_mode, tensor_cores=args.tensor_cores == "on")
     q = pair["quats"]
     f.update_fixed(A, MA)
     f.align(B, MB, q[: 2 * f.batch])
@@ -658,9 +691,10 @@ def run_large(args):
     res = f.align(B, MB, q)
     dt = time.perf_counter() - t0
     print(json.dumps({
-        "metric": "256^3 rotations/s (all-shift maps, 512^3 FFT)", "unit": UNIT, "value": R / dt,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"256^3 pair, {R} rotations",
+        "metric": "256^3 rotations/s (all-shift maps)", "unit": UNIT, "value": R / dt,
+        "higher_is_better": True, "dtype": "f32", "precision": args.precision, "data": "synthetic",
+        "config": {"workload": f"256^3 pair, {R} rotations, {args.precision.upper()}",
+                   "padding": PADDING[args.pad_mode],
                    "fft_classes": [{"fft": list(cp), "rotations": n} for cp, n in f.length_classes()],
                    "batch": f.batch,
                    "device_bytes": f.fixed_bytes + f.workspace_bytes},

@@ -101,14 +101,73 @@ def test_traffic_summary_parser(tmp_path, bench):
     csv_path = tmp_path / "traffic.csv"
     csv_path.write_text("==PROF== preamble\n" + head + "".join(rows))
     out_path = tmp_path / "traffic.json"
-    out = pw.traffic_from_csv(str(csv_path), 2, str(out_path))
+    out = pw.traffic_from_csv(str(csv_path), 2, str(out_path), fft=(200, 200, 256))
     assert out["src_hash"] == bench.kernel_source_hash()
-    st = out["stages"]
+    (c,) = out["classes"]
+    assert c["fft"] == [200, 200, 256]
+    st = c["stages"]
     # the fixed volume's pass before the first resample is left out
     assert set(st) == {"resample", "zmac"}
-    assert st["resample"] == {"launches": 1, "dram_bytes_per_rotation": 2.0e6}
+    assert st["resample"] == {"launches": 1, "dram_bytes_per_rotation": 2.0e6,
+                              "dram_bytes_per_launch_fixed": 0.0}
     assert st["zmac"]["dram_bytes_per_rotation"] == pytest.approx((1.25e9 + 1000) / 2)
     assert json.loads(out_path.read_text()) == out
+    # a second capture of the same launches with one rotation separates the
+    # bytes every launch moves (4 rotations: 1.25 GB; 1 rotation: 0.5 GB); at
+    # other lengths it is kept beside the first class
+    base_rows = [
+        _csv_row(1, "csngf::k_resample(const float2 *)", "dram__bytes_read.sum", "Mbyte", "1.0"),
+        _csv_row(2, "void csngf::k_zmac<200, 0, 0, 0>(const void *)", "dram__bytes_read.sum", "Gbyte", "0.5"),
+    ]
+    rows4 = [
+        _csv_row(1, "csngf::k_mask_counts(const unsigned char *)", "dram__bytes_read.sum", "Mbyte", "4.0"),
+        _csv_row(2, "void csngf::k_zmac<200, 0, 0, 0>(const void *)", "dram__bytes_read.sum", "Gbyte", "1.25"),
+    ]
+    p4, p1 = tmp_path / "t4.csv", tmp_path / "t1.csv"
+    p4.write_text(head + "".join(rows4))
+    p1.write_text(head + "".join(base_rows))
+    out = pw.traffic_from_csv([str(p4)], 4, str(out_path), base_paths=[str(p1)], base_rotations=1,
+                              fft=(200, 200, 200))
+    assert [c["fft"] for c in out["classes"]] == [[200, 200, 256], [200, 200, 200]]
+    z = out["classes"][1]["stages"]["zmac"]
+    assert z["dram_bytes_per_rotation"] == pytest.approx(0.25e9)
+    assert z["dram_bytes_per_launch_fixed"] == pytest.approx(0.25e9)
+    r = out["classes"][1]["stages"]["resample"]   # k_mask_counts counts with the resample stage
+    assert r["dram_bytes_per_rotation"] == pytest.approx(1.0e6) and r["dram_bytes_per_launch_fixed"] == pytest.approx(0.0)
+    # recapturing a class replaces its entry
+    out = pw.traffic_from_csv([str(p4)], 4, str(out_path), fft=(200, 200, 200))
+    assert len(out["classes"]) == 2
+    assert out["classes"][1]["stages"]["zmac"]["dram_bytes_per_launch_fixed"] == 0.0
+
+
+def test_traffic_per_launch_by_class(bench, tmp_path, monkeypatch):
+    """Each launch takes its own class's figures; lengths with no capture take
+    the nearest captured class scaled by the byte model."""
+    dims = (150, 150, 150)
+    d = {"src_hash": bench.kernel_source_hash(), "precision": "fp32", "classes": [
+        {"fft": [200, 200, 200], "stages": {"zmac": {"dram_bytes_per_rotation": 100.0,
+                                                     "dram_bytes_per_launch_fixed": 1000.0}}},
+        {"fft": [200, 200, 256], "stages": {"zmac": {"dram_bytes_per_rotation": 130.0,
+                                                     "dram_bytes_per_launch_fixed": 1300.0}}}]}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.json").write_text(json.dumps(d))
+    h = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    L = [((200, 200, 200), 32), ((200, 200, 200), 8), ((200, 200, 256), 4)]
+    assert bench.launch_traffic("zmac", "fp32", dims, L) == pytest.approx(
+        2 * 1000 + 40 * 100 + 1300 + 4 * 130)
+    assert bench.launch_traffic("fwd_x", "fp32", dims, L) is None
+    assert bench.ncu_traffic("zmac", "bf16", dims, (200, 200, 200)) is None
+    # (200, 256, 200) has as many grid points as (200, 200, 256), its nearest capture
+    pr, fx = bench.ncu_traffic("zmac", "fp32", dims, (200, 256, 200))
+    one = lambda q: bench.stage_bytes(dims, q, 1, "zmac") - bench.stage_bytes(dims, q, 0, "zmac")
+    tile = lambda q: bench.stage_bytes(dims, q, 0, "zmac")
+    assert pr == pytest.approx(130.0 * one((200, 256, 200)) / one((200, 200, 256)))
+    assert fx == pytest.approx(1300.0 * tile((200, 256, 200)) / tile((200, 200, 256)))
+    # the fixed-spectra tile has (Px/2 + 1) Py Pz points: 101*256 against 129*200
+    assert fx == pytest.approx(1300.0 * 101 * 256 / (129 * 200))
 
 
 def test_compare_with_oracle(bench):
