@@ -36,11 +36,12 @@
  *   - Shift sign: C(chi) = sum_x a(x) b(x + chi); shifts are reported as
  *     (chi_z, chi_y, chi_x) in [-(n-1), n-1].
  *   - A shift is valid iff N(chi) >= max(1, ceil(gamma * min(sum M_A,
- *     sum M_hat))).  Masks are 0/1 bytes (nonzero counts as 1).
+ *     sum M_hat))), the product taken in FP64 from the FP32 gamma given.
+ *     Masks are 0/1 bytes (nonzero counts as 1).
  *   - Ties: the larger score wins; equal scores go to the smallest
  *     (chi_z, chi_y, chi_x), then to the smallest rotation index.
  *   - FFT lengths: per axis the smallest of {16, 32, 40, 64, 80, 100, 128,
- *     160, 200, 256, 320, 400, 512} that is >= 2n - 1 (full linear
+ *     160, 192, 200, 216, 256, 320, 400, 512} that is >= 2n - 1 (full linear
  *     correlation), unless set.  With bound-limited padding (the default,
  *     cs_ngf_pad_mode) a call may use shorter lengths; the results are the
  *     same (see cs_ngf_pad_mode).

@@ -52,11 +52,11 @@ CHANNEL_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
 CHANNEL_WEIGHTS = (1.0, 1.0, 1.0, 2.0, 2.0, 2.0)
 MEASURES = ("squared", "unsquared")
 
-SUPPORTED_PADS = (16, 32, 40, 64, 80, 100, 128, 160, 200, 256, 320, 400, 512)
+SUPPORTED_PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512)
 
 
 def auto_pad(n: int) -> int:
-    """Smallest supported 2^a 5^b FFT length >= 2n - 1 (full linear correlation)."""
+    """Smallest supported FFT length (2^a 3^b 5^c) >= 2n - 1 (full linear correlation)."""
     for p in SUPPORTED_PADS:
         if p >= 2 * n - 1:
             return p

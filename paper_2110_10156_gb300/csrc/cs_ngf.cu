@@ -46,7 +46,7 @@ namespace {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                     \
   } while (0)
 
-constexpr int kPads[] = {16, 32, 40, 64, 80, 100, 128, 160, 200, 256, 320, 400, 512};
+constexpr int kPads[] = {16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512};
 
 bool pad_supported(int p) {
   for (int v : kPads)
@@ -146,7 +146,9 @@ struct Stage {
     case 100: { constexpr int PP = 100; CALL; } break;                                  \
     case 128: { constexpr int PP = 128; CALL; } break;                                  \
     case 160: { constexpr int PP = 160; CALL; } break;                                  \
+    case 192: { constexpr int PP = 192; CALL; } break;                                  \
     case 200: { constexpr int PP = 200; CALL; } break;                                  \
+    case 216: { constexpr int PP = 216; CALL; } break;                                  \
     case 256: { constexpr int PP = 256; CALL; } break;                                  \
     case 320: { constexpr int PP = 320; CALL; } break;                                  \
     case 400: { constexpr int PP = 400; CALL; } break;                                  \

@@ -59,21 +59,31 @@ __global__ void k_pack_floating(const float* __restrict__ B, const uint8_t* __re
   }
 }
 
-// sample point p = R (x - c) + c of voxel (x, y, z) per axis (FP32, fixed order)
-__device__ __forceinline__ void sample_axes(const RotMat& R, const Geo& g, int x, int y, int z,
+// The sample point p = R (x - c) + c of voxel (x, y, z), per axis
+// ((R0 dx + R1 dy) + R2 dz) + c in round-to-nearest FP32 without contraction.
+// A resample thread keeps x and y over its z-planes, so the first sum is
+// formed once per thread (SampleRow) and each plane adds its z term in the
+// same order: the same floats as forming the whole sum per voxel.
+struct SampleRow {
+  float s[3];                                   // rn(rn(R_i0 dx) + rn(R_i1 dy))
+};
+__device__ __forceinline__ SampleRow sample_row(const RotMat& R, const Geo& g, int x, int y) {
+  const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1);
+  const float dx = __fsub_rn((float)x, cx), dy = __fsub_rn((float)y, cy);
+  SampleRow sr;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) sr.s[i] = __fadd_rn(__fmul_rn(R.m[3 * i + 0], dx), __fmul_rn(R.m[3 * i + 1], dy));
+  return sr;
+}
+__device__ __forceinline__ void sample_axes(const RotMat& R, const SampleRow& sr, const Geo& g, int z,
                                             AxisSample& ax, AxisSample& ay, AxisSample& az) {
   const float cx = 0.5f * (float)(g.nx - 1), cy = 0.5f * (float)(g.ny - 1),
               cz = 0.5f * (float)(g.nz - 1);
-  const float dx = __fsub_rn((float)x, cx), dy = __fsub_rn((float)y, cy),
-              dz = __fsub_rn((float)z, cz);
+  const float dz = __fsub_rn((float)z, cz);
   float p[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float acc = __fmul_rn(R.m[3 * i + 0], dx);
-    acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 1], dy));
-    acc = __fadd_rn(acc, __fmul_rn(R.m[3 * i + 2], dz));
-    p[i] = __fadd_rn(acc, i == 0 ? cx : (i == 1 ? cy : cz));
-  }
+  for (int i = 0; i < 3; ++i)
+    p[i] = __fadd_rn(__fadd_rn(sr.s[i], __fmul_rn(R.m[3 * i + 2], dz)), i == 0 ? cx : (i == 1 ? cy : cz));
   ax = axis_sample(p[0], g.nx);
   ay = axis_sample(p[1], g.ny);
   az = axis_sample(p[2], g.nz);
@@ -96,9 +106,9 @@ __device__ __forceinline__ uint8_t mask_decision(unsigned bits, float tx, float 
 
 // the rotated mask alone: the same sample point and decision as resample_voxel
 __device__ __forceinline__ uint8_t mask_voxel(const uint8_t* __restrict__ C8, const RotMat& R,
-                                              const Geo& g, int x, int y, int z) {
+                                              const SampleRow& sr, const Geo& g, int z) {
   AxisSample ax, ay, az;
-  sample_axes(R, g, x, y, z, ax, ay, az);
+  sample_axes(R, sr, g, z, ax, ay, az);
   if (!(ax.inside && ay.inside && az.inside)) return 0;
   const int b000 = az.i0 * (g.nx * g.ny) + ay.i0 * g.nx + ax.i0;
   return mask_decision(__ldg(&C8[b000]), ax.t, ay.t, az.t);
@@ -106,10 +116,10 @@ __device__ __forceinline__ uint8_t mask_voxel(const uint8_t* __restrict__ C8, co
 
 __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BP,
                                                const uint8_t* __restrict__ C8, const RotMat& R,
-                                               const Geo& g, int x, int y, int z, float& val,
+                                               const SampleRow& sr, const Geo& g, int z, float& val,
                                                uint8_t& m) {
   AxisSample ax, ay, az;
-  sample_axes(R, g, x, y, z, ax, ay, az);
+  sample_axes(R, sr, g, z, ax, ay, az);
   val = 0.0f;
   m = 0;
   if (ax.inside && ay.inside && az.inside) {
@@ -150,19 +160,23 @@ __device__ __forceinline__ void resample_block(const float2* __restrict__ BP,
   const int y = blockIdx.y * 4 + ty;
   __shared__ int zs[ZB], ys[4][4], xs[4][8], cs[4];
   const RotMat R = rot[r];
+  const SampleRow sr = sample_row(R, g, x, y);
+  const bool xy_ok = x < g.nx && y < g.ny;
+  const long long plane = (long long)g.nx * g.ny;
+  // output index of plane z = zt*ZB + wid, advanced by four planes per group
+  long long idx = (long long)r * g.nvox + (long long)(zt * ZB + wid) * plane + (long long)y * g.nx + x;
   int c = 0;                                   // this thread's mask voxels
 #pragma unroll 1
-  for (int k = 0; k < RZ; ++k) {
+  for (int k = 0; k < RZ; ++k, idx += 4 * plane) {
     const int z = zt * ZB + 4 * k + wid;
     int mk = 0;
-    if (x < g.nx && y < g.ny && z < g.nz) {
+    if (xy_ok && z < g.nz) {
       if constexpr (MONLY) {
-        mk = mask_voxel(C8, R, g, x, y, z);
+        mk = mask_voxel(C8, R, sr, g, z);
       } else {
         float val;
         uint8_t m;
-        resample_voxel(BP, C8, R, g, x, y, z, val, m);
-        const long long idx = (long long)r * g.nvox + ((long long)z * g.ny + y) * g.nx + x;
+        resample_voxel(BP, C8, R, sr, g, z, val, m);
         Bh[idx] = val;
         Mh[idx] = m;
         mk = m;

@@ -147,6 +147,21 @@ struct Dft<2, S> {
 };
 
 template <int S>
+struct Dft<3, S> {
+  __device__ __forceinline__ static void run(float2 (&v)[3]) {
+    constexpr float c1 = (float)ctw::cos2pi(1, 3), s1 = (float)ctw::sin2pi(1, 3);
+    const float2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    const float2 x0 = v[0];
+    v[0] = cadd(x0, t);
+    const float2 a = make_float2(x0.x + c1 * t.x, x0.y + c1 * t.y);
+    const float2 ib = mul_si<S>(make_float2(s1 * d.x, s1 * d.y));   // S i sin(2 pi/3) (x1 - x2)
+    // X1 = a + S i b, X2 = a - S i b
+    v[1] = cadd(a, ib);
+    v[2] = csub(a, ib);
+  }
+};
+
+template <int S>
 struct Dft<4, S> {
   __device__ __forceinline__ static void run(float2 (&v)[4]) {
     float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
@@ -181,7 +196,11 @@ struct Dft<5, S> {
 };
 
 constexpr int first_factor(int R) {
-  return (R % 4 == 0 && R != 4) ? 4 : (R % 2 == 0 && R != 2) ? 2 : (R % 5 == 0 && R != 5) ? 5 : R;
+  return (R % 4 == 0 && R != 4) ? 4
+         : (R % 2 == 0 && R != 2) ? 2
+         : (R % 5 == 0 && R != 5) ? 5
+         : (R % 3 == 0 && R != 3) ? 3
+                                  : R;
 }
 
 // composite R = A * B in registers (same split as the block four-step)
@@ -226,7 +245,9 @@ template <> struct SplitV<80, 0>  { static constexpr int N1 = 8,  N2 = 10; };
 template <> struct SplitV<100, 0> { static constexpr int N1 = 10, N2 = 10; };
 template <> struct SplitV<128, 0> { static constexpr int N1 = 8,  N2 = 16; };
 template <> struct SplitV<160, 0> { static constexpr int N1 = 8,  N2 = 20; };
+template <> struct SplitV<192, 0> { static constexpr int N1 = 12, N2 = 16; };
 template <> struct SplitV<200, 0> { static constexpr int N1 = 10, N2 = 20; };
+template <> struct SplitV<216, 0> { static constexpr int N1 = 12, N2 = 18; };
 template <> struct SplitV<256, 0> { static constexpr int N1 = 16, N2 = 16; };
 template <> struct SplitV<320, 0> { static constexpr int N1 = 16, N2 = 20; };
 template <> struct SplitV<400, 0> { static constexpr int N1 = 16, N2 = 25; };

@@ -132,7 +132,7 @@ __global__ void k_resample(const float2* __restrict__ BP, const uint8_t* __restr
 // the pre-pass that bounds the shifts of a whole call.  Grid: resample_grid.
 __global__ void k_mask_counts(const uint8_t* __restrict__ C8, const RotMat* __restrict__ rot, Geo g,
                               int* __restrict__ msum, int* __restrict__ marg);
-constexpr int kResampleZGroups = 4;            // z-plane groups of 4 per resample block
+constexpr int kResampleZGroups = 8;            // z-plane groups of 4 per resample block
 inline dim3 resample_grid(const Geo& g, int nrot) {
   return dim3((unsigned)((g.nx + 7) / 8), (unsigned)((g.ny + 3) / 4),
               (unsigned)(((g.nz + 4 * kResampleZGroups - 1) / (4 * kResampleZGroups)) * nrot));

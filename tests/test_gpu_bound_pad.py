@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 # supported FFT lengths (include/cs_ngf.h)
-PADS = (16, 32, 40, 64, 80, 100, 128, 160, 200, 256, 320, 400, 512)
+PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512)
 IDENTITY = np.array([1.0, 0.0, 0.0, 0.0])
 
 
@@ -231,3 +231,28 @@ def test_rotations_grouped_by_their_own_lengths(cs):
     np.testing.assert_allclose(sr, sc, rtol=0, atol=1e-4 * np.max(np.abs(sf[fin])))
     s, ri, chi = f.align(dev(p.B), dev(p.MB), p.quats)
     assert ri == int(np.argmax(sc)) and chi == tuple(int(v) for v in sh[ri])
+
+
+# Lengths with a factor 3 (192 = 12 x 16, 216 = 12 x 18: the radix-3 register
+# DFT) on every axis, with full-length inputs: full masks and gamma = 1/4 admit
+# shifts out to 3n/4, so bound-limited padding picks 192 or 216 for n > P/2.
+# gamma is exact in FP32 (the ABI's type) and FP64 (the oracle's), so both
+# sides take the same threshold ceil(gamma min(sum M_A, sum M_hat)).
+RADIX3_CASES = [((104, 10, 12), 0, 192), ((122, 9, 11), 0, 216), ((12, 104, 10), 1, 192),
+                ((9, 122, 11), 1, 216), ((10, 12, 104), 2, 192), ((11, 9, 122), 2, 216)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("dims,axis,want", RADIX3_CASES)
+def test_radix3_lengths_full_length_inputs(cs, dims, axis, want, precision):
+    gamma = 0.25
+    p = synth.small_pair(60 + sum(dims), dims, masks="full", n_rot=2)
+    f = cs.prepare_fixed(dev(p.A), dev(p.MA), gamma=gamma, precision=precision)
+    tau = 1e-4 if precision == "fp32" else 1e-2
+    for q in (IDENTITY, p.quats[1]):
+        gmap = f.score_map(dev(p.B), dev(p.MB), q).cpu().numpy()
+        assert f.pad == expected_pads(p, [q], gamma)
+        assert f.pad[axis] == want and 2 * dims[axis] > want
+        omap, _ = O.score_map(p.A, p.MA, p.B, p.MB, q, gamma=gamma)
+        check_maps(omap, gmap, tau=tau)
+    f.release()

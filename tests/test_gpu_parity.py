@@ -57,6 +57,8 @@ MAP_CASES = [
     ((10, 12, 9), (200, 512, 256)),
     ((7, 9, 8), (32, 400, 512)),
     ((16, 15, 14), (320, 320, 320)),
+    ((9, 10, 8), (192, 216, 192)),          # radix-3 lengths, half-length inputs
+    ((11, 8, 10), (216, 192, 216)),
 ]
 
 

@@ -79,7 +79,9 @@ TC_LENGTH_CASES = [
     ((45, 10, 9), (100, 100, 32)),       # ragged y tail: 100 columns in blocks of 8
     ((60, 8, 10), (128, 16, 32)),
     ((70, 9, 8), (160, 32, 16)),
+    ((96, 8, 9), (192, 16, 32)),         # radix-3 CUDA-core half (12 x 16)
     ((90, 8, 9), (200, 16, 32)),         # the 150^3 workload's z length
+    ((108, 8, 9), (216, 16, 32)),        # 12 x 18
 ]
 
 

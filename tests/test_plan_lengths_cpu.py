@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 # supported FFT lengths (include/cs_ngf.h)
-PADS = (16, 32, 40, 64, 80, 100, 128, 160, 200, 256, 320, 400, 512)
+PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512)
 
 
 @pytest.fixture(scope="module")
@@ -102,15 +102,22 @@ def test_classes_match_the_rule_and_cover_every_rotation(binding, seed):
         k += n
 
 
-def test_the_150_cubed_ranges_give_200_for_most_rotations(binding):
-    """A rotation admitting shifts within +-40 on a 150^3 volume needs 190 <= 200
-    per axis; one reaching +51 on y needs 201, hence 256 on that axis."""
+def test_the_150_cubed_ranges_give_192_to_216(binding):
+    """A rotation admitting shifts within +-40 on a 150^3 volume needs 190 <= 192
+    per axis; one reaching +51 on y needs 201, hence 216 on that axis, and
+    one reaching +45 on x needs 195, hence 200 (the 20 rotations left at 192^3
+    then join that class: cheaper than a class of their own)."""
     dims, max_pad = (150, 150, 150), (320, 320, 320)
     b = np.tile(np.array([149 - 40, 149 + 40] * 3, np.int32), (64, 1))
     b[:20, 3] = 149 + 51
     cls, order = binding.plan_lengths(dims, max_pad, b)
-    assert cls == [((200, 200, 200), 44), ((200, 256, 200), 20)]
+    assert cls == [((192, 192, 192), 44), ((192, 216, 192), 20)]
     assert sorted(order[44:].tolist()) == list(range(20))
+    b[40:, 5] = 149 + 45
+    cls, order = binding.plan_lengths(dims, max_pad, b)
+    want, want_order, _ = mirror(dims, max_pad, b.tolist())
+    assert cls == want and order.tolist() == want_order
+    assert ((192, 192, 200), 44) in cls
 
 
 def test_bad_arguments(binding):
