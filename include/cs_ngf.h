@@ -41,7 +41,7 @@
  *   - Ties: the larger score wins; equal scores go to the smallest
  *     (chi_z, chi_y, chi_x), then to the smallest rotation index.
  *   - FFT lengths: per axis the smallest of {16, 32, 40, 64, 80, 100, 128,
- *     160, 192, 200, 216, 256, 320, 400, 512} that is >= 2n - 1 (full linear
+ *     160, 192, 200, 216, 256, 320, 360, 400, 512} that is >= 2n - 1 (full linear
  *     correlation), unless set.  With bound-limited padding (the default,
  *     cs_ngf_pad_mode) a call may use shorter lengths; the results are the
  *     same (see cs_ngf_pad_mode).

@@ -52,7 +52,7 @@ CHANNEL_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
 CHANNEL_WEIGHTS = (1.0, 1.0, 1.0, 2.0, 2.0, 2.0)
 MEASURES = ("squared", "unsquared")
 
-SUPPORTED_PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512)
+SUPPORTED_PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 360, 400, 512)
 
 
 def auto_pad(n: int) -> int:

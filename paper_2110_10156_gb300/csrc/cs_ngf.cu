@@ -46,7 +46,7 @@ namespace {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                     \
   } while (0)
 
-constexpr int kPads[] = {16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512};
+constexpr int kPads[] = {16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 360, 400, 512};
 
 bool pad_supported(int p) {
   for (int v : kPads)
@@ -151,6 +151,7 @@ struct Stage {
     case 216: { constexpr int PP = 216; CALL; } break;                                  \
     case 256: { constexpr int PP = 256; CALL; } break;                                  \
     case 320: { constexpr int PP = 320; CALL; } break;                                  \
+    case 360: { constexpr int PP = 360; CALL; } break;                                  \
     case 400: { constexpr int PP = 400; CALL; } break;                                  \
     case 512: { constexpr int PP = 512; CALL; } break;                                  \
     default: break;                                                                     \

@@ -250,19 +250,23 @@ template <> struct SplitV<200, 0> { static constexpr int N1 = 10, N2 = 20; };
 template <> struct SplitV<216, 0> { static constexpr int N1 = 12, N2 = 18; };
 template <> struct SplitV<256, 0> { static constexpr int N1 = 16, N2 = 16; };
 template <> struct SplitV<320, 0> { static constexpr int N1 = 16, N2 = 20; };
+template <> struct SplitV<360, 0> { static constexpr int N1 = 18, N2 = 20; };
 template <> struct SplitV<400, 0> { static constexpr int N1 = 16, N2 = 25; };
 template <> struct SplitV<512, 0> { static constexpr int N1 = 16, N2 = 32; };
 template <> struct SplitV<64, 1>  { static constexpr int N1 = 4,  N2 = 16; };
 template <> struct SplitV<80, 1>  { static constexpr int N1 = 4,  N2 = 20; };
 template <> struct SplitV<128, 1> { static constexpr int N1 = 4,  N2 = 32; };
 template <> struct SplitV<160, 1> { static constexpr int N1 = 10, N2 = 16; };
+template <> struct SplitV<192, 1> { static constexpr int N1 = 8,  N2 = 24; };
 template <> struct SplitV<200, 1> { static constexpr int N1 = 8,  N2 = 25; };
+template <> struct SplitV<216, 1> { static constexpr int N1 = 8,  N2 = 27; };
 template <> struct SplitV<256, 1> { static constexpr int N1 = 8,  N2 = 32; };
 template <> struct SplitV<320, 1> { static constexpr int N1 = 10, N2 = 32; };
 template <> struct SplitV<400, 1> { static constexpr int N1 = 20, N2 = 20; };
 // lengths with a second split
 constexpr bool has_alt_split(int N) {
-  return N == 64 || N == 80 || N == 128 || N == 160 || N == 200 || N == 256 || N == 320 || N == 400;
+  return N == 64 || N == 80 || N == 128 || N == 160 || N == 192 || N == 200 || N == 216 || N == 256 ||
+         N == 320 || N == 400;
 }
 template <int N>
 using Split = SplitV<N, 0>;

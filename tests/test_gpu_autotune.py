@@ -28,8 +28,8 @@ def dev(a):
 
 
 # lengths with a second split (include/cs_ngf.h, fft_core.cuh SplitV)
-ALT = {64: (4, 16), 80: (4, 20), 128: (4, 32), 160: (10, 16), 200: (8, 25), 256: (8, 32),
-       320: (10, 32), 400: (20, 20)}
+ALT = {64: (4, 16), 80: (4, 20), 128: (4, 32), 160: (10, 16), 192: (8, 24), 200: (8, 25),
+       216: (8, 27), 256: (8, 32), 320: (10, 32), 400: (20, 20)}
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])

@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 # supported FFT lengths (include/cs_ngf.h)
-PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512)
+PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 360, 400, 512)
 IDENTITY = np.array([1.0, 0.0, 0.0, 0.0])
 
 
@@ -239,7 +239,8 @@ def test_rotations_grouped_by_their_own_lengths(cs):
 # gamma is exact in FP32 (the ABI's type) and FP64 (the oracle's), so both
 # sides take the same threshold ceil(gamma min(sum M_A, sum M_hat)).
 RADIX3_CASES = [((104, 10, 12), 0, 192), ((122, 9, 11), 0, 216), ((12, 104, 10), 1, 192),
-                ((9, 122, 11), 1, 216), ((10, 12, 104), 2, 192), ((11, 9, 122), 2, 216)]
+                ((9, 122, 11), 1, 216), ((10, 12, 104), 2, 192), ((11, 9, 122), 2, 216),
+                ((200, 10, 12), 0, 360), ((10, 12, 200), 2, 360)]
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])

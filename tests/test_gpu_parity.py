@@ -59,6 +59,7 @@ MAP_CASES = [
     ((16, 15, 14), (320, 320, 320)),
     ((9, 10, 8), (192, 216, 192)),          # radix-3 lengths, half-length inputs
     ((11, 8, 10), (216, 192, 216)),
+    ((9, 8, 10), (360, 32, 360)),           # 18 x 20
 ]
 
 

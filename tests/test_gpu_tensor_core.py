@@ -92,11 +92,12 @@ def test_tensor_core_z_pass_every_length(cs, dims, pad):
 
 
 @pytest.mark.parametrize("dims,pad", [((30, 10, 12), (64, 32, 32)), ((60, 8, 10), (128, 16, 32)),
-                                      ((90, 8, 9), (200, 16, 32))])
+                                      ((96, 8, 9), (192, 16, 32)), ((90, 8, 9), (200, 16, 32)),
+                                      ((108, 8, 9), (216, 16, 32))])
 def test_tensor_core_z_pass_alternative_splits(cs, dims, pad):
-    """The second radix split of each length (4 x 16, 4 x 32, 8 x 25) changes
-    the CUDA-core half's block (256, 512 and 400 threads, the last with a
-    half warp)."""
+    """The second radix split of each length (4 x 16, 4 x 32, 8 x 24, 8 x 25,
+    8 x 27) changes the CUDA-core half's block (256, 512, 384, 400 and 432
+    threads, the 400- and 432-thread blocks with a half warp)."""
     p = synth.small_pair(950 + sum(dims), dims, masks="threshold", n_rot=3)
     run_case(cs, p, pad, "full", autotune="alternative", expect_pz=pad[0])
 

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 # supported FFT lengths (include/cs_ngf.h)
-PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 400, 512)
+PADS = (16, 32, 40, 64, 80, 100, 128, 160, 192, 200, 216, 256, 320, 360, 400, 512)
 
 
 @pytest.fixture(scope="module")
