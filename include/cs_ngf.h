@@ -273,7 +273,7 @@ int64_t cs_ngf_launch_count(void);
  * the same inputs, using the same kernels, one rotation at a time.  It
  * allocates nothing: no cudaMalloc, no cudaFree and no allocating library
  * routine.  All scratch memory is a single file-scope device array of
- * CS_NGF_NOALLOC_SCRATCH_BYTES bytes (about 13.7 MiB).  Every GPU that loads
+ * CS_NGF_NOALLOC_SCRATCH_BYTES bytes (about 13.9 MiB).  Every GPU that loads
  * this library holds that array until the process exits.
  *   A, maskA, B, maskB  device, [nz][ny][nx] float32 / uint8
  *   dims                host {nz, ny, nx}, each in [2, CS_NGF_NOALLOC_MAX_DIM];
@@ -298,7 +298,7 @@ int64_t cs_ngf_launch_count(void);
  * wrong results: serialise them.
  * Errors: EINVAL, ECUDA (detail in cs_ngf_last_error()). */
 #define CS_NGF_NOALLOC_MAX_DIM 32
-#define CS_NGF_NOALLOC_SCRATCH_BYTES 14321408
+#define CS_NGF_NOALLOC_SCRATCH_BYTES 14583552
 cs_ngf_status cs_ngf_score_rotations_noalloc(const float* A, const uint8_t* maskA, const float* B,
                                              const uint8_t* maskB, const int32_t dims[3],
                                              float eps, float gamma, const double* quats,

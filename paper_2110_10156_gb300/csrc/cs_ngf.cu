@@ -181,7 +181,7 @@ void free_handle(cs_ngf_fixed* f) {
   cudaFree(f->UV);
   cudaFree(f->Bh);
   cudaFree(f->Mh);
-  cudaFree(f->BP);
+  cudaFree(f->BQ);
   cudaFree(f->C8);
   cudaFree(f->F02);
   cudaFree(f->F13);
@@ -418,14 +418,14 @@ cs_ngf_status run_transforms(cs_ngf_fixed* f, int nb, float* map, cudaStream_t s
   return CS_NGF_OK;
 }
 
-// (B, M_B) -> f->BP, f->C8, shared by every rotation of the call
+// (B, M_B) -> f->BQ, f->C8, shared by every rotation of the call
 cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st) {
-  { Stage sp(f, 0, st); k_pack_floating<<<512, 256, 0, st>>>(B, MB, f->g, f->BP, f->C8); }
+  { Stage sp(f, 0, st); k_pack_floating<<<512, 256, 0, st>>>(B, MB, f->g, f->BQ, f->C8); }
   return check_launch("pack");
 }
 
 // score nb rotations whose matrices are at rot (device), with the floating
-// volume already packed in f->BP, f->C8; results to out_score[nb], out_shift[nb][3]
+// volume already packed in f->BQ, f->C8; results to out_score[nb], out_shift[nb][3]
 cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float* out_score,
                                int32_t* out_shift, float* map, cudaStream_t st, bool tune = false) {
   const Geo& g = f->g;
@@ -435,7 +435,7 @@ cs_ngf_status score_batch_ptrs(cs_ngf_fixed* f, const RotMat* rot, int nb, float
   CS_CUDA(cudaMemsetAsync(f->margB, 0, sizeof(int) * nmarg * nb, st));
   {
     Stage sp(f, 0, st);
-    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BP, f->C8, rot, g, f->Bh, f->Mh, f->msum, f->margB);
+    k_resample<<<resample_grid(g, nb), 128, 0, st>>>(f->BQ, f->C8, rot, g, f->Bh, f->Mh, f->msum, f->margB);
   }
   if (cs_ngf_status s = check_launch("resample")) return s;
   const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
@@ -874,7 +874,7 @@ Sizes sizes_for(const int32_t dims[3], const int pad[3], int measure, int precis
   z.fixed_f13 = nf * E1;
   z.zx_elems = (tensor_cores && precision != CS_NGF_FP32) ? (Px / 2 + 1) * Py * Pz : 0;
   z.per_rot = (z.f02_elems + z.f13_elems + z.zx_elems) * sizeof(float2) + nvox * 5;
-  z.shared_ws = nvox * (sizeof(float2) + 1);                       // BP, C8
+  z.shared_ws = nvox * (sizeof(float4) + 1);                       // BQ, C8
   z.uv_elems = (2 * nch + 1) * (Px / 2 + 1) * Py * Pz;
   return z;
 }
@@ -1058,7 +1058,7 @@ cs_ngf_status cs_ngf_prepare_fixed(const float* A, const uint8_t* maskA, const i
   CS_TRYC(dalloc(&f->UV, uv_elems));
   CS_TRYC(dalloc(&f->Bh, (size_t)batch * g.nvox));
   CS_TRYC(dalloc(&f->Mh, (size_t)batch * g.nvox));
-  CS_TRYC(dalloc(&f->BP, (size_t)g.nvox));
+  CS_TRYC(dalloc(&f->BQ, (size_t)g.nvox));
   CS_TRYC(dalloc(&f->C8, (size_t)g.nvox));
   CS_TRYC(dalloc(&f->F02, std::max((size_t)batch * f->f02_elems, sz.fixed_f02)));
   CS_TRYC(dalloc(&f->F13, std::max((size_t)batch * f->f13_elems, sz.fixed_f13)));
@@ -1198,7 +1198,7 @@ cs_ngf_status cs_ngf_resample(cs_ngf_fixed* f, const float* B, const uint8_t* ma
   CS_CUDA(cudaMemsetAsync(f->msum, 0, sizeof(int), st));
   const Geo& g = f->g;
   if (cs_ngf_status s = pack_floating(f, B, maskB, st)) return s;
-  k_resample<<<resample_grid(g, 1), 128, 0, st>>>(f->BP, f->C8, f->rot_d, g, Bhat, Mhat, f->msum, nullptr);
+  k_resample<<<resample_grid(g, 1), 128, 0, st>>>(f->BQ, f->C8, f->rot_d, g, Bhat, Mhat, f->msum, nullptr);
   return check_launch("resample");
 }
 

@@ -36,19 +36,22 @@ __device__ __forceinline__ float lerp_rn(float a, float b, float t) {
 }  // namespace
 
 // The floating volume as the resample reads it, prepared once per call and
-// shared by every rotation: x-pairs BP[i] = (B[i], B[i+1]), so the two x
-// corners of a cell come in one 8-byte load, and corner codes C8[i] whose bit
-// k is M_B at corner (dx, dy, dz) = (k & 1, (k >> 1) & 1, k >> 2) of the cell
-// with base voxel i, so the eight mask corners come in one byte.  A cell base
-// is never on a far face (axis_sample clamps i0 <= n - 2); those entries hold 0.
+// shared by every rotation: BQ[i] = (B[i], B[i+1], B[i+sy], B[i+sy+1]), the
+// x-pairs of rows y and y+1, so the four corners of a cell's z-face come in
+// one 16-byte load (one sector instead of two), and corner codes C8[i] whose
+// bit k is M_B at corner (dx, dy, dz) = (k & 1, (k >> 1) & 1, k >> 2) of the
+// cell with base voxel i, so the eight mask corners come in one byte.  A cell
+// base is never on a far face (axis_sample clamps i0 <= n - 2); entries past
+// the volume hold 0.
 __global__ void k_pack_floating(const float* __restrict__ B, const uint8_t* __restrict__ MB, Geo g,
-                                float2* __restrict__ BP, uint8_t* __restrict__ C8) {
+                                float4* __restrict__ BQ, uint8_t* __restrict__ C8) {
   const int sy = g.nx, sz = g.nx * g.ny;          // volumes hold < 2^31 voxels
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.nvox;
        i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / sz);
-    const bool in_x = x + 1 < g.nx;
-    BP[i] = make_float2(B[i], in_x ? B[i + 1] : 0.0f);
+    const bool in_x = x + 1 < g.nx, in_y = y + 1 < g.ny;
+    BQ[i] = make_float4(B[i], in_x ? B[i + 1] : 0.0f, in_y ? B[i + sy] : 0.0f,
+                        in_x && in_y ? B[i + sy + 1] : 0.0f);
     unsigned bits = 0;
     if (in_x && y + 1 < g.ny && z + 1 < g.nz) {
       const int o[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
@@ -114,7 +117,7 @@ __device__ __forceinline__ uint8_t mask_voxel(const uint8_t* __restrict__ C8, co
   return mask_decision(__ldg(&C8[b000]), ax.t, ay.t, az.t);
 }
 
-__device__ __forceinline__ void resample_voxel(const float2* __restrict__ BP,
+__device__ __forceinline__ void resample_voxel(const float4* __restrict__ BQ,
                                                const uint8_t* __restrict__ C8, const RotMat& R,
                                                const SampleRow& sr, const Geo& g, int z, float& val,
                                                uint8_t& m) {
@@ -125,8 +128,9 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BP,
   if (ax.inside && ay.inside && az.inside) {
     const int sy = g.nx, sz = g.nx * g.ny;        // volumes hold < 2^31 voxels
     const int b000 = az.i0 * sz + ay.i0 * sy + ax.i0;
-    const float2 c00 = __ldg(&BP[b000]), c01 = __ldg(&BP[b000 + sy]);
-    const float2 c10 = __ldg(&BP[b000 + sz]), c11 = __ldg(&BP[b000 + sz + sy]);
+    const float4 q0 = __ldg(&BQ[b000]), q1 = __ldg(&BQ[b000 + sz]);   // z-faces z0, z0 + 1
+    const float2 c00 = make_float2(q0.x, q0.y), c01 = make_float2(q0.z, q0.w);
+    const float2 c10 = make_float2(q1.x, q1.y), c11 = make_float2(q1.z, q1.w);
     const unsigned bits = __ldg(&C8[b000]);
     // intensity: lerps along x, y, z, exact at t = 0 and t = 1 so that
     // quarter turns reproduce the voxels bit for bit
@@ -146,7 +150,7 @@ __device__ __forceinline__ void resample_voxel(const float2* __restrict__ BP,
 // Grid: (x tiles, y tiles, z tiles * rotations).
 // MONLY: only the rotated mask, counted (no volumes written)
 template <bool MONLY>
-__device__ __forceinline__ void resample_block(const float2* __restrict__ BP,
+__device__ __forceinline__ void resample_block(const float4* __restrict__ BQ,
                                                const uint8_t* __restrict__ C8,
                                                const RotMat* __restrict__ rot, const Geo& g,
                                                float* __restrict__ Bh, uint8_t* __restrict__ Mh,
@@ -176,7 +180,7 @@ __device__ __forceinline__ void resample_block(const float2* __restrict__ BP,
       } else {
         float val;
         uint8_t m;
-        resample_voxel(BP, C8, R, sr, g, z, val, m);
+        resample_voxel(BQ, C8, R, sr, g, z, val, m);
         Bh[idx] = val;
         Mh[idx] = m;
         mk = m;
@@ -221,10 +225,10 @@ __device__ __forceinline__ void resample_block(const float2* __restrict__ BP,
 }
 
 __global__ void __launch_bounds__(128)
-k_resample(const float2* __restrict__ BP, const uint8_t* __restrict__ C8,
+k_resample(const float4* __restrict__ BQ, const uint8_t* __restrict__ C8,
            const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh, uint8_t* __restrict__ Mh,
            int* __restrict__ msum, int* __restrict__ marg) {
-  resample_block<false>(BP, C8, rot, g, Bh, Mh, msum, marg);
+  resample_block<false>(BQ, C8, rot, g, Bh, Mh, msum, marg);
 }
 
 __global__ void __launch_bounds__(128)

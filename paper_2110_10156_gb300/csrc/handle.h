@@ -50,7 +50,7 @@ struct cs_ngf_fixed {
   float2* UV = nullptr;
   float* Bh = nullptr;
   uint8_t* Mh = nullptr;
-  float2* BP = nullptr;        // x-pairs (B[i], B[i+1]) of the current call
+  float4* BQ = nullptr;        // x-pairs of rows y, y+1 (B[i], B[i+1], B[i+sy], B[i+sy+1]) of the current call
   uint8_t* C8 = nullptr;       // corner codes of M_B of the current call
   float2* F02 = nullptr;
   float2* F13 = nullptr;
@@ -102,7 +102,7 @@ namespace detail {
 cs_ngf_status fail(cs_ngf_status s, const std::string& msg);
 // host FP64 quaternions -> FP32 matrices in f->rot_d[0..R)
 cs_ngf_status upload_rotations(cs_ngf_fixed* f, const double* quats, int R, cudaStream_t st);
-// (B, M_B) -> f->BP, f->C8 for the following score calls
+// (B, M_B) -> f->BQ, f->C8 for the following score calls
 cs_ngf_status pack_floating(cs_ngf_fixed* f, const float* B, const uint8_t* MB, cudaStream_t st);
 // Bound-limited padding (pad_mode CS_NGF_PAD_BOUND): the R uploaded
 // rotations of the floating volume packed by pack_floating, grouped into

@@ -120,11 +120,11 @@ __device__ __forceinline__ unsigned long long make_key(float s, unsigned lin) {
 // [trilinear M_B >= 0.5] inside [0, n-1]^3 (+-1e-4).  The sample point and the
 // mask decision use round-to-nearest FP32 operations in a fixed order (no
 // contraction), so the decision is reproducible bit for bit.  B and M_B are
-// read as the x-pairs and corner codes k_pack_floating prepares (BP, C8: nvox
-// entries each).
+// read as the row-pair table and corner codes k_pack_floating prepares (BQ,
+// C8: nvox entries each).
 __global__ void k_pack_floating(const float* __restrict__ B, const uint8_t* __restrict__ MB, Geo g,
-                                float2* __restrict__ BP, uint8_t* __restrict__ C8);
-__global__ void k_resample(const float2* __restrict__ BP, const uint8_t* __restrict__ C8,
+                                float4* __restrict__ BQ, uint8_t* __restrict__ C8);
+__global__ void k_resample(const float4* __restrict__ BQ, const uint8_t* __restrict__ C8,
                            const RotMat* __restrict__ rot, Geo g, float* __restrict__ Bh,
                            uint8_t* __restrict__ Mh, int* __restrict__ msum, int* __restrict__ marg);
 // The rotated masks alone, counted into msum and marg as k_resample counts

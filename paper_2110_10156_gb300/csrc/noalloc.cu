@@ -40,7 +40,7 @@ constexpr size_t kF02Bytes = align256(kF02Elems * 8);
 constexpr size_t kF13Bytes = align256(kF13Elems * 8);
 constexpr size_t kVolBytes = align256((size_t)kNaMaxDim * kNaMaxDim * kNaMaxDim * 4);
 constexpr size_t kMaskBytes = align256((size_t)kNaMaxDim * kNaMaxDim * kNaMaxDim);
-constexpr size_t kBPBytes = align256((size_t)kNaMaxDim * kNaMaxDim * kNaMaxDim * 8);
+constexpr size_t kBQBytes = align256((size_t)kNaMaxDim * kNaMaxDim * kNaMaxDim * 16);
 constexpr size_t kC8Bytes = align256((size_t)kNaMaxDim * kNaMaxDim * kNaMaxDim);
 constexpr size_t kTwBytes = align256((size_t)3 * kNaMaxPad * 8);
 constexpr size_t kMiscBytes = 256;   // msum[2] (A, B), thr, key, rotation matrix
@@ -50,8 +50,8 @@ constexpr size_t kOffF02 = kOffUV + kUVBytes;
 constexpr size_t kOffF13 = kOffF02 + kF02Bytes;
 constexpr size_t kOffBh = kOffF13 + kF13Bytes;
 constexpr size_t kOffMh = kOffBh + kVolBytes;
-constexpr size_t kOffBP = kOffMh + kMaskBytes;
-constexpr size_t kOffC8 = kOffBP + kBPBytes;
+constexpr size_t kOffBQ = kOffMh + kMaskBytes;
+constexpr size_t kOffC8 = kOffBQ + kBQBytes;
 constexpr size_t kOffTw = kOffC8 + kC8Bytes;
 constexpr size_t kOffMisc = kOffTw + kTwBytes;
 constexpr size_t kScratchBytes = kOffMisc + kMiscBytes;
@@ -237,7 +237,7 @@ extern "C" cs_ngf_status cs_ngf_score_rotations_noalloc(
   float2* F13 = (float2*)(base + kOffF13);
   float* Bh = (float*)(base + kOffBh);
   uint8_t* Mh = (uint8_t*)(base + kOffMh);
-  float2* BP = (float2*)(base + kOffBP);
+  float4* BQ = (float4*)(base + kOffBQ);
   uint8_t* C8 = (uint8_t*)(base + kOffC8);
   float2* tw = (float2*)(base + kOffTw);
   Misc* misc = (Misc*)(base + kOffMisc);
@@ -259,7 +259,7 @@ extern "C" cs_ngf_status cs_ngf_score_rotations_noalloc(
   NA_DISPATCH(g.Pz, launch_prep_z<PP>(F13, UV, twz, g, st));
   if (cs_ngf_status s = na_launched("fixed transforms")) return s;
 
-  k_pack_floating<<<64, 256, 0, st>>>(B, maskB, g, BP, C8);
+  k_pack_floating<<<64, 256, 0, st>>>(B, maskB, g, BQ, C8);
   if (cs_ngf_status s = na_launched("pack")) return s;
   const double pvol = (double)g.Px * (double)g.Py * (double)g.Pz;
   for (int r = 0; r < R; ++r) {
@@ -268,7 +268,7 @@ extern "C" cs_ngf_status cs_ngf_score_rotations_noalloc(
     RotMat m;
     for (int i = 0; i < 9; ++i) m.m[i] = (float)Rm[i];
     k_na_set_rot<<<1, 1, 0, st>>>(m, misc);                 // also zeroes the sum and key
-    k_resample<<<resample_grid(g, 1), 128, 0, st>>>(BP, C8, &misc->rot, g, Bh, Mh, &misc->msum[1], nullptr);
+    k_resample<<<resample_grid(g, 1), 128, 0, st>>>(BQ, C8, &misc->rot, g, Bh, Mh, &misc->msum[1], nullptr);
     k_na_threshold<<<1, 1, 0, st>>>(misc, gamma, pvol);
     NA_DISPATCH(g.Px, launch_fwd_x<PP>(Bh, Mh, F02, twx, g, 1, st));
     NA_DISPATCH(g.Py, launch_fwd_y<PP>(F02, F13, twy, g, 1, st));
