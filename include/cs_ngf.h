@@ -151,8 +151,9 @@ typedef struct {
   int32_t tensor_cores; /* 1 (cs_ngf_default_config): in the BF16 and FP16 forms the z pass
                         runs the forward z-axis DFT of the NGF channel fields on the tensor
                         cores (BF16 / FP16 operands, FP32 accumulation; Eq. 7-8 unchanged)
-                        wherever the z length is at most 200 (16 ... 200) and the block's
-                        operands fit in shared memory (at 200: z extent at most 160); the
+                        wherever the z length is at most 216 (16 ... 216) and the block's
+                        operands fit in shared memory (at 200 and 216: z extent at most
+                        160); the
                         mask field and every inverse transform stay FP32 on the CUDA cores.
                         The handle then holds one more per-rotation buffer (the spectral sum
                         X, (Px/2+1) Py Pz complex values).  0: the CUDA-core FFT for every
