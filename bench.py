@@ -194,10 +194,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+_SOURCE_HASH = {}
+
+
 def kernel_source_hash():
     """Hash of the sources the scoring kernels and their launches are built
     from (the serving loop, search driver and allocation-free entry point are
-    left out: they launch the same kernels)."""
+    left out: they launch the same kernels); computed once per process."""
+    if ROOT in _SOURCE_HASH:
+        return _SOURCE_HASH[ROOT]
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_10156_gb300", "csrc")
     keep = ("fft_core.cuh", "kernels.cuh", "passes.cuh", "elem.cu", "cs_ngf.cu", "handle.h",
@@ -206,7 +211,8 @@ def kernel_source_hash():
         if fn in keep or (fn.startswith("passes_") and fn.endswith(".cu")):
             with open(os.path.join(csrc, fn), "rb") as fh:
                 h.update(fh.read())
-    return h.hexdigest()[:16]
+    _SOURCE_HASH[ROOT] = h.hexdigest()[:16]
+    return _SOURCE_HASH[ROOT]
 
 
 def ncu_traffic(stage: str, precision: str = "fp32", dims=None, pad=None):
